@@ -1,0 +1,196 @@
+"""Seeded synthetic inputs shared by the oracle tests, the CUDA-path tests and the benchmark.
+
+This module holds no arithmetic of the multigrid method itself: it only draws random numbers and
+evaluates the closed-form fields (cosine modes, Gaussian bumps, smoothed noise) that the paper's
+workloads are shaped like. Both sides of every parity test receive the identical float64 arrays
+produced here.
+
+Random numbers come from SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014), used in counter mode: element k of a stream with key K is
+mix64(K + (k + 1) * GAMMA). The 53 high bits of each 64-bit output give a uniform double in [0, 1).
+The generator is written out here from its published definition so that results do not depend on
+the numpy version installed on a machine.
+
+Array convention everywhere in this project: C order with x fastest, so a 2D field has numpy shape
+(ny, nx) and is indexed [j, i]; a 3D field has shape (nz, ny, nx) and is indexed [l, j, i]. Cell
+centres are x_i = (i + 1/2) h for 0-based i (the paper's x_i = (i - 1/2) h with 1-based i).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# stream tags: one independent stream per (seed, purpose)
+TAG_NOISE = 1
+TAG_SOURCE = 2
+TAG_KAPPA = 3
+TAG_TARGET = 4
+TAG_SIZES = 5
+TAG_COEF = 6
+TAG_NORMAL = 7
+TAG_INIT = 8
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def stream_key(seed: int, tag: int) -> np.uint64:
+    """64-bit key of the stream (seed, tag), scrambled so that nearby seeds give unrelated keys."""
+    with np.errstate(over="ignore"):
+        base = np.array([(int(seed) * 256 + int(tag)) & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64)
+        return _mix64(base + GAMMA)[0]
+
+
+def uniform(seed: int, tag: int, count: int, offset: int = 0) -> np.ndarray:
+    """`count` uniform doubles in [0, 1) from stream (seed, tag), starting at element `offset`."""
+    key = stream_key(seed, tag)
+    k = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = _mix64(key + k * GAMMA)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, tag: int, count: int) -> np.ndarray:
+    """`count` standard normal doubles by the Box-Muller transform of pairs of uniforms."""
+    m = (count + 1) // 2
+    u = uniform(seed, tag, 2 * m)
+    u1 = 1.0 - u[0::2]  # in (0, 1]
+    u2 = u[1::2]
+    rad = np.sqrt(-2.0 * np.log(u1))
+    z = np.empty(2 * m)
+    z[0::2] = rad * np.cos(2.0 * math.pi * u2)
+    z[1::2] = rad * np.sin(2.0 * math.pi * u2)
+    return z[:count]
+
+
+def cell_centres(n: int, h: float | None = None) -> np.ndarray:
+    """Cell-centre coordinates (i + 1/2) h, i = 0..n-1, on [0, n h]; h defaults to 1/n."""
+    if h is None:
+        h = 1.0 / n
+    return (np.arange(n, dtype=np.float64) + 0.5) * h
+
+
+def _grids(shape, h):
+    axes = [cell_centres(n, h) for n in shape]  # numpy axis order (z, y, x)
+    return np.meshgrid(*axes, indexing="ij")
+
+
+def cos_mode(shape, h=None) -> np.ndarray:
+    """prod over axes of cos(pi * x_axis): the slowest Neumann eigenmode on [0,1]^d."""
+    if h is None:
+        h = 1.0 / shape[-1]
+    grids = _grids(shape, h)
+    out = np.ones(shape)
+    for g in grids:
+        out *= np.cos(math.pi * g)
+    return out
+
+
+def noisy_cos_mode(shape, seed: int, amplitude: float = 1e-2) -> np.ndarray:
+    """cos-mode initial field plus `amplitude` * U(-1, 1) noise (heat workloads)."""
+    n = int(np.prod(shape))
+    noise = 2.0 * uniform(seed, TAG_NOISE, n) - 1.0
+    return cos_mode(shape) + amplitude * noise.reshape(shape)
+
+
+def gaussian_sum(shape, seed: int, tag: int, count: int, sigma: float,
+                 amp_lo: float = -1.0, amp_hi: float = 1.0) -> np.ndarray:
+    """sum_k a_k exp(-|x - c_k|^2 / (2 sigma^2)), centres c_k ~ U(0,1)^d, a_k ~ U(amp_lo, amp_hi)."""
+    d = len(shape)
+    draws = uniform(seed, tag, count * (d + 1))
+    centres = draws[: count * d].reshape(count, d)  # columns in physical order x, y, (z)
+    amps = amp_lo + (amp_hi - amp_lo) * draws[count * d:]
+    h = 1.0 / shape[-1]
+    axes_phys = [cell_centres(n, h) for n in reversed(shape)]  # x, y, (z)
+    out = np.zeros(shape)
+    for k in range(count):
+        # separable evaluation: product over axes of 1D Gaussians
+        factors = [np.exp(-((axes_phys[a] - centres[k, a]) ** 2) / (2.0 * sigma * sigma))
+                   for a in range(d)]
+        term = factors[0]
+        for a in range(1, d):
+            term = np.multiply.outer(factors[a], term)  # builds (.., y, x) order
+        out += amps[k] * term
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# workload recipes (the shapes and value distributions of the paper's heat / Helmholtz problems)
+# ---------------------------------------------------------------------------------------------
+
+def heat2d_small(n: int = 128, seed: int = 0):
+    """128^2 heat: Neumann, kappa 1, dt 1e-3, 10 steps, u0 = cos mode + 1e-2 noise, no source."""
+    shape = (n, n)
+    return dict(shape=shape, h=1.0 / n, dt=1e-3, nsteps=10, kappa=1.0,
+                u0=noisy_cos_mode(shape, seed), fsrc=None)
+
+
+def heat2d_large(n: int = 8192, seed: int = 1, nsteps: int = 20):
+    """8192^2 heat: Neumann, kappa 1, dt 1e-4, 20 steps, u0 = cos mode + noise,
+    source = 16 Gaussians (sigma 0.02, centres U(0,1)^2, amplitudes U(-1,1))."""
+    shape = (n, n)
+    return dict(shape=shape, h=1.0 / n, dt=1e-4, nsteps=nsteps, kappa=1.0,
+                u0=noisy_cos_mode(shape, seed),
+                fsrc=gaussian_sum(shape, seed, TAG_SOURCE, 16, 0.02))
+
+
+def heat3d(n: int = 512, seed: int = 2, nsteps: int = 10):
+    """512^3 heat, 7-point: Neumann, kappa 1, dt 1e-4, 10 steps, u0 = 3D cos mode + noise."""
+    shape = (n, n, n)
+    return dict(shape=shape, h=1.0 / n, dt=1e-4, nsteps=nsteps, kappa=1.0,
+                u0=noisy_cos_mode(shape, seed), fsrc=None)
+
+
+def smoothed_normal(shape, seed: int, passes: int = 3) -> np.ndarray:
+    """N(0,1) field smoothed by `passes` damped-Jacobi averages f <- f/2 + (1/8) sum_4 nbrs with
+    mirrored (zero-flux) edges. Input preparation only; not the solver's smoother."""
+    f = normal(seed, TAG_NORMAL, int(np.prod(shape))).reshape(shape)
+    for _ in range(passes):
+        p = np.pad(f, 1, mode="edge")
+        nb = p[:-2, 1:-1] + p[2:, 1:-1] + p[1:-1, :-2] + p[1:-1, 2:]
+        f = 0.5 * f + 0.125 * nb
+    return f
+
+
+def batched_helmholtz(count: int = 96, seed: int = 3, sizes=(64, 128, 256, 512, 1024, 2048)):
+    """Independent 2D problems (I - dt kappa Lap) u = f: n uniform over `sizes`, kappa ~ U(0.5, 2),
+    dt uniform over {1e-4, 1e-3}, Neumann, f = N(0,1) smoothed by 3 Jacobi passes."""
+    draws = uniform(seed, TAG_SIZES, 3 * count)
+    problems = []
+    for p in range(count):
+        n = sizes[min(int(draws[3 * p] * len(sizes)), len(sizes) - 1)]
+        kappa = 0.5 + 1.5 * draws[3 * p + 1]
+        dt = 1e-4 if draws[3 * p + 2] < 0.5 else 1e-3
+        problems.append(dict(n=n, kappa=float(kappa), dt=dt, seed=seed * 1000 + p))
+    return problems
+
+
+def batched_problem_rhs(problem) -> np.ndarray:
+    n = problem["n"]
+    return smoothed_normal((n, n), problem["seed"])
+
+
+def adjoint_heat(n: int = 1024, nsteps: int = 50):
+    """1024^2 heat with varying diffusivity kappa = 1 + 0.5 tanh(sum of 8 Gaussians, sigma 0.1,
+    amplitudes U(-2,2)); u0 cos mode + noise; source 16 Gaussians (sigma 0.05); target 4 Gaussians
+    (sigma 0.15). Loss ||u_T - u_target||^2."""
+    shape = (n, n)
+    g = gaussian_sum(shape, 4, TAG_KAPPA, 8, 0.1, -2.0, 2.0)
+    return dict(shape=shape, h=1.0 / n, dt=1e-3, nsteps=nsteps,
+                kappa=1.0 + 0.5 * np.tanh(g),
+                u0=noisy_cos_mode(shape, 4),
+                fsrc=gaussian_sum(shape, 5, TAG_SOURCE, 16, 0.05),
+                target=gaussian_sum(shape, 6, TAG_TARGET, 4, 0.15))
+
+
+def random_field(shape, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """Uniform U(lo, hi) field (random initial guesses and random test operands)."""
+    return lo + (hi - lo) * uniform(seed, TAG_INIT, int(np.prod(shape))).reshape(shape)

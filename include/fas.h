@@ -1,0 +1,145 @@
+/*
+ * fas.h -- C ABI of the GB300 matrix-free FAS multigrid library (libfasmg.so).
+ *
+ * The library solves  A u = f  with  A u = alpha u - beta div_h(kappa grad_h u)  on a uniform
+ * cell-centred grid (Sec. 2.1-2.2 of the paper: cells x_i = (i - 1/2) h, one ghost layer, the
+ * 5-point / 7-point operator L_h), by the FAS multigrid of Algorithm 1 with its recursive
+ * multilevel remark, X-MCGS smoothing (Sec. 2.3, Eqs. FCGS-1..4; 3D sets of Appendix B), and the
+ * average restriction / piecewise-constant prolongation of Appendix C.
+ *
+ * Conventions shared by every entry point
+ *   Layout     Fields are dense C-order arrays with x fastest: 2D index j*nx + i, 3D index
+ *              (l*ny + j)*nx + i, 0-based. No ghost cells are stored; boundary conditions are
+ *              folded into the point equations (homogeneous Neumann: ghost = adjacent cell;
+ *              homogeneous Dirichlet: ghost = -adjacent cell, Eqs. boundry1-2).
+ *   Ownership  Field pointers passed to fas_vcycle / fas_solve / fas_heat_run are DEVICE pointers
+ *              owned by the caller and must stay valid until the call returns (the library may
+ *              enqueue work on the stream that reads them; calls return after that work is
+ *              complete unless stated otherwise). The library owns only the coarse levels and
+ *              scratch it allocates in fas_create and frees in fas_destroy.
+ *              The *_host entry points take HOST pointers and do the copies themselves.
+ *   Streams    All device work is enqueued on the cudaStream_t given to fas_create (NULL = the
+ *              legacy default stream).
+ *   Errors     Every call returns a fas_status; nothing aborts or throws. fas_last_error() gives a
+ *              thread-local message for the last failing call on the calling thread.
+ *   Threads    A fas_ctx must not be used by two threads at once.
+ */
+#ifndef FAS_H
+#define FAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FAS_OK = 0,
+  FAS_EINVAL = 1,        /* invalid argument (sizes not powers of two, h <= 0, nu < 0, ...)  */
+  FAS_ENOMEM = 2,        /* device or host allocation failed                                  */
+  FAS_ENOTCONV = 3,      /* kmax cycles done without reaching tol; info is filled            */
+  FAS_ENONFINITE = 4,    /* residual became NaN/Inf                                           */
+  FAS_ETIMEOUT = 5,      /* a bounded device-side wait expired                               */
+  FAS_ECUDA = 6,         /* a CUDA runtime call failed (message in fas_last_error)            */
+  FAS_EUNSUPPORTED = 7   /* valid request this build does not implement                       */
+} fas_status;
+
+typedef enum { FAS_BC_NEUMANN = 0, FAS_BC_DIRICHLET = 1 } fas_bc;
+typedef enum { FAS_FP64 = 0, FAS_MIXED = 1 } fas_precision;
+
+/* Problem and solver parameters (the paper's user parameters s, kMax, tol, meshLevel of
+ * Algorithm 1's symbol table, plus the operator of Sec. 2.2 generalised to alpha, beta, kappa). */
+typedef struct {
+  int dim;               /* 2 or 3                                                             */
+  int n[3];              /* cells along x, y, z (n[2] ignored in 2D); each a power of two >= 2  */
+  double h;              /* uniform spacing on every axis (Sec. 2.1: h = (b-a)/M = (d-c)/N)      */
+  double alpha, beta;    /* A u = alpha u - beta div(kappa grad u); heat step: alpha 1, beta dt  */
+  const double* kappa;   /* DEVICE pointer to a per-cell diffusivity field, or NULL            */
+  double kappa_const;    /* diffusivity used when kappa == NULL                                 */
+  int bc[6];             /* fas_bc per face: x_lo, x_hi, y_lo, y_hi, z_lo, z_hi                  */
+  int nu1, nu2;          /* pre- and post-smoothing sweeps (the paper's s; default 2, 2)        */
+  int nu_coarse;         /* sweeps on the coarsest level (paper: s); <= 0 means nu1             */
+  int kmax;              /* maximum V-cycles per solve (kMax)                                  */
+  int coarsest;          /* cells along the shortest axis of the coarsest level (>= 2)          */
+  int coarse_exact;      /* 0: smooth the coarsest level (paper); 1: dense direct solve         */
+  double tol;            /* stopping tolerance                                                 */
+  int tol_relative;      /* 1: ||f - A u||_2 <= tol ||f||_2 ; 0: h^{d/2}||f - A u||_2 <= tol    */
+  int precision;         /* fas_precision: FP64, or FP32 inner cycles in FP64 refinement        */
+  int inner_cycles;      /* FAS_MIXED: FP32 V-cycles per refinement step (default 1)          */
+  int use_graph;         /* 1: capture repeated launch sequences in CUDA graphs (default 1)     */
+} fas_params;
+
+/* Per-solve report. res0/res are ||f - A u||_2 before the first and after the last cycle
+ * (the paper's h-weighted value when tol_relative == 0); rel = res / ||f||_2; rho is the mean
+ * contraction (res/res0)^(1/cycles). */
+typedef struct {
+  int cycles;
+  int converged;
+  double res0, res, rel, rho;
+} fas_info;
+
+typedef struct fas_ctx fas_ctx;
+
+/* Fill *p with the defaults: V(2,2), kmax 20, coarsest 4, tol 1e-10 relative, FP64, Neumann. */
+void fas_default_params(fas_params* p);
+
+/* Validate the parameters, build the level hierarchy (Sec. 2.1: each coarser grid halves every
+ * axis and doubles h) and allocate its device storage. stream is a cudaStream_t (may be NULL).
+ * Errors: FAS_EINVAL (bad sizes or parameters), FAS_ENOMEM, FAS_ECUDA. */
+fas_status fas_create(const fas_params* p, void* stream, fas_ctx** out);
+
+/* Free everything fas_create allocated. NULL is accepted. */
+fas_status fas_destroy(fas_ctx* ctx);
+
+/* Number of levels (finest = 0) and the cell count of a level. */
+int fas_num_levels(const fas_ctx* ctx);
+
+/* Exactly one V-cycle in place on device field u with right-hand side f (one pass of Algorithm
+ * 1's k loop with recursion), then the residual norm into info (may be NULL). */
+fas_status fas_vcycle(fas_ctx* ctx, double* u, const double* f, fas_info* info);
+
+/* V-cycles on u (initial guess, overwritten) until the residual test of Algorithm 1 passes or
+ * kmax cycles are done. FP64 or mixed precision per the context's parameters.
+ * Returns FAS_ENOTCONV (info filled) if tol was not reached, FAS_ENONFINITE on NaN/Inf. */
+fas_status fas_solve(fas_ctx* ctx, double* u, const double* f, fas_info* info);
+
+/* Backward-Euler heat stepping (the paper's time-dependent use, the new step overwriting the
+ * old): for n in 0..nsteps-1 solve (I - dt div(kappa grad)) u^{n+1} = u^n + dt fsrc from the
+ * initial guess u^n. The context must have alpha = 1 and beta = dt. fsrc may be NULL (no
+ * source). infos (may be NULL) receives one fas_info per step. */
+fas_status fas_heat_run(fas_ctx* ctx, double* u, const double* fsrc, double dt, int nsteps,
+                        fas_info* infos);
+
+/* fas_heat_run with HOST buffers: copies u (in/out) and fsrc to the device, runs, copies u back. */
+fas_status fas_heat_run_host(fas_ctx* ctx, double* u_host, const double* fsrc_host, double dt,
+                             int nsteps, fas_info* infos);
+
+/* --- single operators, for testing each kernel against the oracle ---------------------------- */
+
+/* out = f - A u on level `level` (Sec. 2.2, r = f - L_h p), norm2 (may be NULL) = ||out||_2.
+ * Level 0 fields are the caller's; level > 0 operates on caller fields of that level's size. */
+fas_status fas_residual(fas_ctx* ctx, int level, const double* u, const double* f, double* out,
+                        double* norm2);
+
+/* `sweeps` X-MCGS sweeps in place on u of level `level` (Sec. 2.3 / Appendix B). */
+fas_status fas_smooth(fas_ctx* ctx, int level, double* u, const double* f, int sweeps);
+
+/* uc = R(u) (Appendix C average of 2^d children), u of level `level`, uc of level + 1. */
+fas_status fas_restrict(fas_ctx* ctx, int level, const double* u, double* uc);
+
+/* u += P(c) (Appendix C piecewise-constant prolongation), c of level + 1, u of level `level`. */
+fas_status fas_prolong_add(fas_ctx* ctx, int level, double* u, const double* c);
+
+/* Thread-local message describing the last error on this thread ("" if none). */
+const char* fas_last_error(void);
+
+/* Number of kernel launches this context has issued since creation or the last reset (for the
+ * benchmark's launch count; a captured graph counts each of its kernel nodes per replay). */
+long long fas_launch_count(const fas_ctx* ctx, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FAS_H */

@@ -1,0 +1,291 @@
+"""Python binding of libfasmg.so, the GB300 matrix-free FAS multigrid library.
+
+Argument marshalling only: every step of the solver runs in the library's CUDA kernels. The functions
+carry the C-ABI names of include/fas.h and take torch CUDA tensors (float64, contiguous, C order with
+x fastest) for device fields. There is no CPU fallback: if the library has not been built, load()
+raises.
+
+    import paper_2510_11152_gb300 as fas
+    p = fas.fas_default_params(); p.dim = 2; p.n[:2] = (1024, 1024); p.h = 1 / 1024
+    ctx = fas.fas_create(p)
+    info = fas.fas_solve(ctx, u, f)
+    fas.fas_destroy(ctx)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB as LIB_PATH
+
+__all__ = [
+    "FasError", "fas_params", "fas_info", "load", "fas_default_params", "fas_create", "fas_destroy",
+    "fas_num_levels", "fas_vcycle", "fas_solve", "fas_heat_run", "fas_heat_run_host", "fas_residual",
+    "fas_smooth", "fas_restrict", "fas_prolong_add", "fas_last_error", "fas_launch_count", "Solver",
+]
+
+FAS_OK, FAS_EINVAL, FAS_ENOMEM, FAS_ENOTCONV, FAS_ENONFINITE, FAS_ETIMEOUT, FAS_ECUDA, FAS_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["FAS_OK", "FAS_EINVAL", "FAS_ENOMEM", "FAS_ENOTCONV", "FAS_ENONFINITE", "FAS_ETIMEOUT",
+                "FAS_ECUDA", "FAS_EUNSUPPORTED"]
+FAS_BC_NEUMANN, FAS_BC_DIRICHLET = 0, 1
+FAS_FP64, FAS_MIXED = 0, 1
+
+
+class fas_params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("kappa", ctypes.c_void_p),
+        ("kappa_const", ctypes.c_double), ("bc", ctypes.c_int * 6), ("nu1", ctypes.c_int),
+        ("nu2", ctypes.c_int), ("nu_coarse", ctypes.c_int), ("kmax", ctypes.c_int),
+        ("coarsest", ctypes.c_int), ("coarse_exact", ctypes.c_int), ("tol", ctypes.c_double),
+        ("tol_relative", ctypes.c_int), ("precision", ctypes.c_int), ("inner_cycles", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+    ]
+
+
+class fas_info(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("converged", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res", ctypes.c_double), ("rel", ctypes.c_double), ("rho", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FasError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = fas_last_error() if _lib is not None else ""
+        super().__init__("%s failed: %s (%s)" % (where, STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+
+
+def load(path: str | None = None):
+    """Load libfasmg.so (built by paper_2510_11152_gb300.build) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libfasmg.so not built (%s); run paper_2510_11152_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    sig = {
+        "fas_default_params": (None, [ctypes.POINTER(fas_params)]),
+        "fas_create": (_I, [ctypes.POINTER(fas_params), _P, ctypes.POINTER(_P)]),
+        "fas_destroy": (_I, [_P]),
+        "fas_num_levels": (_I, [_P]),
+        "fas_vcycle": (_I, [_P, _P, _P, ctypes.POINTER(fas_info)]),
+        "fas_solve": (_I, [_P, _P, _P, ctypes.POINTER(fas_info)]),
+        "fas_heat_run": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(fas_info)]),
+        "fas_heat_run_host": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(fas_info)]),
+        "fas_residual": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(_D)]),
+        "fas_smooth": (_I, [_P, _I, _P, _P, _I]),
+        "fas_restrict": (_I, [_P, _I, _P, _P]),
+        "fas_prolong_add": (_I, [_P, _I, _P, _P]),
+        "fas_last_error": (ctypes.c_char_p, []),
+        "fas_launch_count": (ctypes.c_longlong, [_P, _I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, where):
+    if status != FAS_OK:
+        raise FasError(status, where)
+
+
+def _dev(t, what, numel=None):
+    """Device pointer of a float64 contiguous CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("%s must be contiguous float64" % what)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (what, t.numel(), numel))
+    return t.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def fas_last_error() -> str:
+    return load().fas_last_error().decode()
+
+
+def fas_default_params() -> fas_params:
+    p = fas_params()
+    load().fas_default_params(ctypes.byref(p))
+    return p
+
+
+class _Ctx:
+    """Owns a fas_ctx* together with the parameters and the tensors it must keep alive."""
+
+    def __init__(self, handle, params, keep):
+        self.handle = handle
+        self.params = params
+        self.keep = keep
+
+    @property
+    def cells(self):
+        p = self.params
+        return p.n[0] * p.n[1] * (p.n[2] if p.dim == 3 else 1)
+
+    def level_cells(self, level):
+        p = self.params
+        c = (p.n[0] >> level) * (p.n[1] >> level)
+        return c * ((p.n[2] >> level) if p.dim == 3 else 1)
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.fas_destroy(self.handle)
+            self.handle = None
+
+
+def fas_create(params: fas_params, stream=None, kappa=None) -> _Ctx:
+    """fas_create; `kappa` (optional float64 CUDA tensor) sets params.kappa."""
+    lib = load()
+    if kappa is not None:
+        params.kappa = _dev(kappa, "kappa")
+    out = _P()
+    _check(lib.fas_create(ctypes.byref(params), _stream_handle(stream), ctypes.byref(out)), "fas_create")
+    return _Ctx(out, params, [kappa])
+
+
+def fas_destroy(ctx: _Ctx) -> None:
+    if ctx.handle:
+        _check(load().fas_destroy(ctx.handle), "fas_destroy")
+        ctx.handle = None
+
+
+def fas_num_levels(ctx: _Ctx) -> int:
+    return load().fas_num_levels(ctx.handle)
+
+
+def _info_call(fn, ctx, where, *args, allow_notconv=False):
+    info = fas_info()
+    st = fn(ctx.handle, *args, ctypes.byref(info))
+    if not (allow_notconv and st == FAS_ENOTCONV):
+        _check(st, where)
+    return info
+
+
+def fas_vcycle(ctx: _Ctx, u, f) -> fas_info:
+    n = ctx.cells
+    return _info_call(load().fas_vcycle, ctx, "fas_vcycle", _dev(u, "u", n), _dev(f, "f", n))
+
+
+def fas_solve(ctx: _Ctx, u, f, allow_notconv=False) -> fas_info:
+    n = ctx.cells
+    return _info_call(load().fas_solve, ctx, "fas_solve", _dev(u, "u", n), _dev(f, "f", n),
+                      allow_notconv=allow_notconv)
+
+
+def fas_heat_run(ctx: _Ctx, u, fsrc, dt: float, nsteps: int):
+    n = ctx.cells
+    infos = (fas_info * max(nsteps, 1))()
+    st = load().fas_heat_run(ctx.handle, _dev(u, "u", n), _dev(fsrc, "fsrc", n), float(dt), int(nsteps), infos)
+    _check(st, "fas_heat_run")
+    return [infos[k] for k in range(nsteps)]
+
+
+def fas_heat_run_host(ctx: _Ctx, u_host, fsrc_host, dt: float, nsteps: int):
+    """Host numpy float64 arrays (u_host updated in place)."""
+    import numpy as np
+    n = ctx.cells
+    for a, what in ((u_host, "u_host"), (fsrc_host, "fsrc_host")):
+        if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n):
+            raise TypeError("%s must be a C-contiguous float64 array of %d elements" % (what, n))
+    infos = (fas_info * max(nsteps, 1))()
+    fptr = None if fsrc_host is None else fsrc_host.ctypes.data
+    st = load().fas_heat_run_host(ctx.handle, u_host.ctypes.data, fptr, float(dt), int(nsteps), infos)
+    _check(st, "fas_heat_run_host")
+    return [infos[k] for k in range(nsteps)]
+
+
+def fas_residual(ctx: _Ctx, level: int, u, f, out=None) -> float:
+    n = ctx.level_cells(level)
+    norm = _D()
+    _check(load().fas_residual(ctx.handle, level, _dev(u, "u", n), _dev(f, "f", n), _dev(out, "out", n),
+                               ctypes.byref(norm)), "fas_residual")
+    return norm.value
+
+
+def fas_smooth(ctx: _Ctx, level: int, u, f, sweeps: int) -> None:
+    n = ctx.level_cells(level)
+    _check(load().fas_smooth(ctx.handle, level, _dev(u, "u", n), _dev(f, "f", n), int(sweeps)), "fas_smooth")
+
+
+def fas_restrict(ctx: _Ctx, level: int, u, uc) -> None:
+    _check(load().fas_restrict(ctx.handle, level, _dev(u, "u", ctx.level_cells(level)),
+                               _dev(uc, "uc", ctx.level_cells(level + 1))), "fas_restrict")
+
+
+def fas_prolong_add(ctx: _Ctx, level: int, u, c) -> None:
+    _check(load().fas_prolong_add(ctx.handle, level, _dev(u, "u", ctx.level_cells(level)),
+                                  _dev(c, "c", ctx.level_cells(level + 1))), "fas_prolong_add")
+
+
+def fas_launch_count(ctx: _Ctx, reset: bool = False) -> int:
+    return load().fas_launch_count(ctx.handle, 1 if reset else 0)
+
+
+def make_params(shape, h, alpha=1.0, beta=1.0, kappa_const=1.0, bc=None, **kw) -> fas_params:
+    """fas_params for a numpy-order shape ((ny, nx) or (nz, ny, nx)); keyword overrides by field."""
+    p = fas_default_params()
+    dim = len(shape)
+    p.dim = dim
+    phys = list(reversed(shape)) + [1] * (3 - dim)
+    for a in range(3):
+        p.n[a] = int(phys[a])
+    p.h = float(h)
+    p.alpha = float(alpha)
+    p.beta = float(beta)
+    p.kappa_const = float(kappa_const)
+    if bc is not None:
+        for k, v in enumerate(bc):
+            p.bc[k] = int(v)
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError("fas_params has no field %s" % k)
+        setattr(p, k, v)
+    return p
+
+
+class Solver:
+    """Convenience owner of a context: Solver(shape, h, ...).solve(u, f)."""
+
+    def __init__(self, shape, h, kappa=None, stream=None, **kw):
+        self.shape = tuple(shape)
+        self.ctx = fas_create(make_params(self.shape, h, **kw), stream=stream, kappa=kappa)
+
+    def vcycle(self, u, f):
+        return fas_vcycle(self.ctx, u, f)
+
+    def solve(self, u, f, allow_notconv=False):
+        return fas_solve(self.ctx, u, f, allow_notconv=allow_notconv)
+
+    def heat_run(self, u, fsrc, dt, nsteps):
+        return fas_heat_run(self.ctx, u, fsrc, dt, nsteps)
+
+    @property
+    def levels(self):
+        return fas_num_levels(self.ctx)
+
+    def close(self):
+        fas_destroy(self.ctx)

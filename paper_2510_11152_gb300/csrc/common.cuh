@@ -1,0 +1,144 @@
+// common.cuh -- level descriptors and the per-point arithmetic shared by every kernel.
+//
+// Operator (Sec. 2.2 generalised): A u = alpha u - beta div_h(kappa grad_h u) on cells of width h.
+// Boundary conditions are folded into each boundary cell's point equation: multiplying the cell's
+// equation by h^2,
+//     D u_c - sum_{interior faces f} w_f u_nb = h^2 f_c,      w_f = beta kappa_f,
+//     D = alpha h^2 + sum_f m_f w_f,   m_f = 1 interior face, 0 Neumann face (ghost = cell),
+//                                      2 Dirichlet face (ghost = -cell).
+// With constant kappa every cell of the same "boundary class" (which faces of the box it touches)
+// has the same D, so the kernels look up per-class constants:
+//     smoother (Eqs. FCGS-1..4)   u_c <- a[cls] * N + b[cls] * f_c,   a = beta kappa / D, b = h^2 / D
+//     residual (Sec. 2.2)         r_c  = f_c - d[cls] u_c + c N,       d = D / h^2,       c = beta kappa / h^2
+// where N is the plain sum of the existing neighbours. For alpha = beta = kappa = 1 in the interior
+// the smoother is (sum of 4 neighbours + h^2 f) / (4 + h^2), the paper's update.
+// With a per-cell kappa the face weights w_f (kappa_f = mean of the two cells) and 1/D, D/h^2 are
+// stored per cell on every level.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fasmg {
+
+constexpr int kMaxLevels = 24;
+constexpr int kClasses = 64;  // 2^(2*dim) boundary classes, dim <= 3
+
+template <typename T>
+struct LevelDesc {
+  int nx, ny, nz;  // cells per axis (nz = 1 in 2D)
+  int varkappa;    // 1: use the per-cell arrays below
+  T h2, ih2;       // h^2, 1/h^2
+  T c;             // beta kappa / h^2 (constant kappa)
+  const T* wx;     // beta kappa_f of the face between cells i and i+1, stored at cell i (0 at i = nx-1)
+  const T* wy;     // same along y (0 at j = ny-1)
+  const T* wz;     // same along z (0 at l = nz-1)
+  const T* rD;     // 1 / D
+  const T* Dh;     // D / h^2
+  T a[kClasses], b[kClasses], d[kClasses];
+};
+
+// boundary class: bit 0 x_lo, 1 x_hi, 2 y_lo, 3 y_hi, 4 z_lo, 5 z_hi
+template <int DIM>
+__device__ __forceinline__ int bclass(int i, int j, int l, int nx, int ny, int nz) {
+  int fl = (i == 0) | ((i == nx - 1) << 1) | ((j == 0) << 2) | ((j == ny - 1) << 3);
+  if (DIM == 3) fl |= ((l == 0) << 4) | ((l == nz - 1) << 5);
+  return fl;
+}
+
+// Sum of the existing neighbours of cell (i, j, l) at linear index idx (constant kappa).
+template <typename T, int DIM>
+__device__ __forceinline__ T nbsum(const T* __restrict__ u, int64_t idx, int i, int j, int l, int nx,
+                                   int ny, int nz) {
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  T w = i > 0 ? u[idx - 1] : T(0);
+  T e = i < nx - 1 ? u[idx + 1] : T(0);
+  T s = j > 0 ? u[idx - sy] : T(0);
+  T n = j < ny - 1 ? u[idx + sy] : T(0);
+  T acc = (w + e) + (s + n);
+  if (DIM == 3) {
+    T bo = l > 0 ? u[idx - sz] : T(0);
+    T to = l < nz - 1 ? u[idx + sz] : T(0);
+    acc = acc + (bo + to);
+  }
+  return acc;
+}
+
+// Weighted neighbour sum sum_f w_f u_nb (per-cell kappa).
+template <typename T, int DIM>
+__device__ __forceinline__ T nbsum_w(const T* __restrict__ u, const LevelDesc<T>& L, int64_t idx, int i,
+                                     int j, int l) {
+  const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny;
+  T acc = T(0);
+  if (i > 0) acc = fma(L.wx[idx - 1], u[idx - 1], acc);
+  if (i < L.nx - 1) acc = fma(L.wx[idx], u[idx + 1], acc);
+  if (j > 0) acc = fma(L.wy[idx - sy], u[idx - sy], acc);
+  if (j < L.ny - 1) acc = fma(L.wy[idx], u[idx + sy], acc);
+  if (DIM == 3) {
+    if (l > 0) acc = fma(L.wz[idx - sz], u[idx - sz], acc);
+    if (l < L.nz - 1) acc = fma(L.wz[idx], u[idx + sz], acc);
+  }
+  return acc;
+}
+
+// Gauss-Seidel point update of cell (i, j, l): the new value from the current neighbours.
+template <typename T, int DIM>
+__device__ __forceinline__ T point_update(const T* __restrict__ u, const T* __restrict__ f,
+                                          const LevelDesc<T>& L, int64_t idx, int i, int j, int l) {
+  if (L.varkappa) {
+    T nw = nbsum_w<T, DIM>(u, L, idx, i, j, l);
+    return fma(L.h2, f[idx], nw) * L.rD[idx];
+  }
+  const int cls = bclass<DIM>(i, j, l, L.nx, L.ny, L.nz);
+  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz);
+  return fma(L.a[cls], nb, L.b[cls] * f[idx]);
+}
+
+// (A u) at cell (i, j, l).
+template <typename T, int DIM>
+__device__ __forceinline__ T apply_point(const T* __restrict__ u, const LevelDesc<T>& L, int64_t idx, int i,
+                                         int j, int l) {
+  if (L.varkappa) {
+    T nw = nbsum_w<T, DIM>(u, L, idx, i, j, l);
+    return fma(L.Dh[idx], u[idx], -L.ih2 * nw);
+  }
+  const int cls = bclass<DIM>(i, j, l, L.nx, L.ny, L.nz);
+  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz);
+  return fma(L.d[cls], u[idx], -L.c * nb);
+}
+
+// Residual f - A u at cell (i, j, l).
+template <typename T, int DIM>
+__device__ __forceinline__ T residual_point(const T* __restrict__ u, const T* __restrict__ f,
+                                            const LevelDesc<T>& L, int64_t idx, int i, int j, int l) {
+  if (L.varkappa) {
+    T nw = nbsum_w<T, DIM>(u, L, idx, i, j, l);
+    return fma(L.ih2, nw, fma(-L.Dh[idx], u[idx], f[idx]));
+  }
+  const int cls = bclass<DIM>(i, j, l, L.nx, L.ny, L.nz);
+  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz);
+  return fma(L.c, nb, fma(-L.d[cls], u[idx], f[idx]));
+}
+
+// Block-wide sum of one double per thread; result valid in thread 0. blockDim.x <= 1024.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double warp_part[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();  // protect warp_part against a previous use
+  if (lane == 0) warp_part[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? warp_part[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace fasmg

@@ -1,0 +1,57 @@
+// context.h -- host-side state of a solver context (shared between the C-ABI translation units).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fas.h"
+#include "common.cuh"
+
+namespace fasmg {
+
+// Level hierarchy of one value type: descriptors (host and device copies) and device buffers.
+//   u[l], f[l], u0[l] : solution, right-hand side and restricted start of level l >= 1
+//                       (for the float hierarchy of mixed precision also level 0: e and r32)
+//   r[l]              : residual scratch of level l
+template <typename T>
+struct Hier {
+  int nlev = 0;
+  int switch_level = 0;  // levels >= switch_level run inside the single-CTA kernel
+  std::vector<LevelDesc<T>> desc;
+  LevelDesc<T>* d_desc = nullptr;
+  std::vector<T*> u, f, r, u0;
+  T** d_u = nullptr;
+  T** d_f = nullptr;
+  T** d_r = nullptr;
+  T** d_u0 = nullptr;
+  T* cinv = nullptr;
+  std::vector<void*> owned;  // every device allocation above
+  bool allocated = false;
+};
+
+struct LevelShape {
+  int nx, ny, nz;
+  double h;
+  int64_t cells() const { return (int64_t)nx * ny * nz; }
+};
+
+}  // namespace fasmg
+
+struct fas_ctx {
+  fas_params p;
+  cudaStream_t stream = nullptr;
+  int sm_count = 148;
+  int nlev = 0;
+  std::vector<fasmg::LevelShape> shape;
+  fasmg::Hier<double> h64;
+  fasmg::Hier<float> h32;
+  bool singular = false;
+  double* partials = nullptr;  // per-block partial sums
+  int max_blocks = 0;
+  double* d_scalar = nullptr;  // small device scalars
+  double* h_scalar = nullptr;  // pinned host mirror
+  double* b = nullptr;         // heat-step right-hand side (fine, float64)
+  double* fproj = nullptr;     // mean-free copy of f for singular problems
+  long long launches = 0;
+};

@@ -1,0 +1,758 @@
+// fas_api.cu -- C-ABI entry points, level hierarchy set-up and the host-side FAS driver.
+//
+// The V-cycle follows Algorithm 1 with the recursion of the remark after it: on every level
+// nu1 X-MCGS sweeps, the residual r = f - A u, u_c = R(u) and f_c = R(r) + A_c u_c (the tau
+// correction; f_c overwrites R(r) in place as in the paper's reuse of r0), the coarse problem,
+// u += P(u_c - R(u)_start), nu2 sweeps. Levels too small to fill the GPU run inside one CTA.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "basic_kernels.cuh"
+#include "context.h"
+
+using namespace fasmg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+fas_status fail(fas_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define CUDA_TRY(call)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(FAS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));               \
+  } while (0)
+
+#define STATUS_TRY(call)            \
+  do {                              \
+    fas_status s_ = (call);         \
+    if (s_ != FAS_OK) return s_;    \
+  } while (0)
+
+bool is_pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+constexpr int kBlock = 256;
+constexpr int kCoarseThreads = 1024;
+constexpr int64_t kSwitchCells2D = 16384;  // levels at or below this size run in one CTA
+constexpr int64_t kSwitchCells3D = 4096;
+
+int grid_for(const fas_ctx* c, int64_t work) {
+  int64_t g = (work + kBlock - 1) / kBlock;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, c->max_blocks));
+}
+
+// ---------------------------------------------------------------------------------------------
+// level descriptors
+// ---------------------------------------------------------------------------------------------
+
+// boundary multiplicity of a face: 0 Neumann (ghost = cell), 2 Dirichlet (ghost = -cell)
+int bc_mult(int kind) { return kind == FAS_BC_DIRICHLET ? 2 : 0; }
+
+template <typename T>
+LevelDesc<T> make_desc(const fas_params& p, const LevelShape& s) {
+  LevelDesc<T> L;
+  std::memset(&L, 0, sizeof(L));
+  L.nx = s.nx;
+  L.ny = s.ny;
+  L.nz = s.nz;
+  L.varkappa = p.kappa != nullptr;
+  const double h2 = s.h * s.h;
+  L.h2 = (T)h2;
+  L.ih2 = (T)(1.0 / h2);
+  const double bk = p.beta * p.kappa_const;
+  L.c = (T)(bk / h2);
+  const int nfaces = 2 * p.dim;
+  for (int cls = 0; cls < kClasses; ++cls) {
+    double m = 0.0;
+    for (int face = 0; face < nfaces; ++face) {
+      const bool boundary = (cls >> face) & 1;
+      m += boundary ? bc_mult(p.bc[face]) : 1.0;
+    }
+    const double D = p.alpha * h2 + bk * m;
+    L.a[cls] = (T)(D != 0.0 ? bk / D : 0.0);
+    L.b[cls] = (T)(D != 0.0 ? h2 / D : 0.0);
+    L.d[cls] = (T)(D / h2);
+  }
+  return L;
+}
+
+template <typename T, typename U>
+fas_status dev_alloc(Hier<T>& H, U** ptr, int64_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (size_t)std::max<int64_t>(count, 1) * sizeof(U));
+  if (e != cudaSuccess) return fail(FAS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  H.owned.push_back(q);
+  *ptr = (U*)q;
+  return FAS_OK;
+}
+
+template <typename T>
+void free_hier(Hier<T>& H) {
+  for (void* q : H.owned) cudaFree(q);
+  H.owned.clear();
+  H.u.clear();
+  H.f.clear();
+  H.r.clear();
+  H.u0.clear();
+  H.d_desc = nullptr;
+  H.cinv = nullptr;
+  H.allocated = false;
+}
+
+// Dense matrix of the coarsest operator (h^-2 scaled like A), assembled from the descriptor, then
+// inverted (pseudo-inverse through A + J/n when the problem is singular).
+fas_status coarse_inverse(const fas_ctx* c, const LevelShape& s, const std::vector<double>& wx,
+                          const std::vector<double>& wy, const std::vector<double>& wz,
+                          const std::vector<double>& Dh, std::vector<double>& inv) {
+  const int n = (int)s.cells();
+  if (n > 1024) return fail(FAS_EUNSUPPORTED, "coarse_exact: coarsest level above 1024 cells");
+  const fas_params& p = c->p;
+  const LevelDesc<double> L = make_desc<double>(p, s);
+  std::vector<double> M((size_t)n * n, 0.0);
+  const int dim = p.dim;
+  for (int l = 0; l < s.nz; ++l)
+    for (int j = 0; j < s.ny; ++j)
+      for (int i = 0; i < s.nx; ++i) {
+        const int q = (l * s.ny + j) * s.nx + i;
+        const int cls = (i == 0) | ((i == s.nx - 1) << 1) | ((j == 0) << 2) | ((j == s.ny - 1) << 3) |
+                        (dim == 3 ? (((l == 0) << 4) | ((l == s.nz - 1) << 5)) : 0);
+        const bool var = p.kappa != nullptr;
+        M[(size_t)q * n + q] = var ? Dh[q] : L.d[cls];
+        auto off = [&](int nb, double w) { M[(size_t)q * n + nb] -= w / (s.h * s.h); };
+        const double bk = p.beta * p.kappa_const;
+        if (i > 0) off(q - 1, var ? wx[q - 1] : bk);
+        if (i < s.nx - 1) off(q + 1, var ? wx[q] : bk);
+        if (j > 0) off(q - s.nx, var ? wy[q - s.nx] : bk);
+        if (j < s.ny - 1) off(q + s.nx, var ? wy[q] : bk);
+        if (dim == 3) {
+          if (l > 0) off(q - s.nx * s.ny, var ? wz[q - s.nx * s.ny] : bk);
+          if (l < s.nz - 1) off(q + s.nx * s.ny, var ? wz[q] : bk);
+        }
+      }
+  if (c->singular)
+    for (auto& v : M) v += 1.0 / n;
+  // Gauss-Jordan with partial pivoting on [M | I]
+  inv.assign((size_t)n * n, 0.0);
+  for (int q = 0; q < n; ++q) inv[(size_t)q * n + q] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(M[(size_t)r * n + col]) > std::fabs(M[(size_t)piv * n + col])) piv = r;
+    if (M[(size_t)piv * n + col] == 0.0) return fail(FAS_EINVAL, "coarse_exact: singular coarsest matrix");
+    if (piv != col)
+      for (int k = 0; k < n; ++k) {
+        std::swap(M[(size_t)piv * n + k], M[(size_t)col * n + k]);
+        std::swap(inv[(size_t)piv * n + k], inv[(size_t)col * n + k]);
+      }
+    const double d = M[(size_t)col * n + col];
+    for (int k = 0; k < n; ++k) {
+      M[(size_t)col * n + k] /= d;
+      inv[(size_t)col * n + k] /= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double fct = M[(size_t)r * n + col];
+      if (fct == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        M[(size_t)r * n + k] -= fct * M[(size_t)col * n + k];
+        inv[(size_t)r * n + k] -= fct * inv[(size_t)col * n + k];
+      }
+    }
+  }
+  if (c->singular)
+    for (auto& v : inv) v -= 1.0 / n;
+  return FAS_OK;
+}
+
+// Build one hierarchy: descriptors for every level, buffers when `buffers`, variable-kappa arrays.
+template <typename T>
+fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers) {
+  const fas_params& p = c->p;
+  H.nlev = c->nlev;
+  H.desc.clear();
+  for (int l = 0; l < c->nlev; ++l) H.desc.push_back(make_desc<T>(p, c->shape[l]));
+  const int64_t sw_cells = p.dim == 2 ? kSwitchCells2D : kSwitchCells3D;
+  H.switch_level = c->nlev - 1;
+  for (int l = 0; l < c->nlev; ++l)
+    if (c->shape[l].cells() <= sw_cells) {
+      H.switch_level = l;
+      break;
+    }
+  // per-cell diffusivity: kappa on every level (cell averages), then weights per level
+  std::vector<double> cwx, cwy, cwz, cDh;  // coarsest level, for the dense inverse
+  if (p.kappa) {
+    double* kap = nullptr;
+    const double* kprev = p.kappa;
+    for (int l = 0; l < c->nlev; ++l) {
+      const LevelShape& s = c->shape[l];
+      const int64_t n = s.cells();
+      if (l > 0) {
+        void* q = nullptr;
+        CUDA_TRY(cudaMalloc(&q, n * sizeof(double)));
+        H.owned.push_back(q);
+        kap = (double*)q;
+        const LevelShape& sf = c->shape[l - 1];
+        if (p.dim == 2)
+          k_restrict<double, 2><<<grid_for(c, n), kBlock, 0, c->stream>>>(kap, nullptr, nullptr, kprev, nullptr,
+                                                                          sf.nx, sf.ny, sf.nz);
+        else
+          k_restrict<double, 3><<<grid_for(c, n), kBlock, 0, c->stream>>>(kap, nullptr, nullptr, kprev, nullptr,
+                                                                          sf.nx, sf.ny, sf.nz);
+        kprev = kap;
+      }
+      T *wx, *wy, *wz, *rD, *Dh;
+      STATUS_TRY(dev_alloc(H, &wx, n));
+      STATUS_TRY(dev_alloc(H, &wy, n));
+      STATUS_TRY(dev_alloc(H, &wz, p.dim == 3 ? n : 1));
+      STATUS_TRY(dev_alloc(H, &rD, n));
+      STATUS_TRY(dev_alloc(H, &Dh, n));
+      const int4 lo = make_int4(bc_mult(p.bc[0]), bc_mult(p.bc[2]), p.dim == 3 ? bc_mult(p.bc[4]) : 0, 0);
+      const int4 hi = make_int4(bc_mult(p.bc[1]), bc_mult(p.bc[3]), p.dim == 3 ? bc_mult(p.bc[5]) : 0, 0);
+      if (p.dim == 2)
+        k_kappa_weights<T, 2><<<grid_for(c, n), kBlock, 0, c->stream>>>(wx, wy, wz, rD, Dh, kprev, s.nx, s.ny,
+                                                                         s.nz, p.alpha, p.beta, s.h, lo, hi);
+      else
+        k_kappa_weights<T, 3><<<grid_for(c, n), kBlock, 0, c->stream>>>(wx, wy, wz, rD, Dh, kprev, s.nx, s.ny,
+                                                                         s.nz, p.alpha, p.beta, s.h, lo, hi);
+      CUDA_TRY(cudaGetLastError());
+      H.desc[l].wx = wx;
+      H.desc[l].wy = wy;
+      H.desc[l].wz = wz;
+      H.desc[l].rD = rD;
+      H.desc[l].Dh = Dh;
+      if (l == c->nlev - 1 && p.coarse_exact) {
+        // weights of the coarsest level in float64 for the dense inverse
+        std::vector<double> kh(n);
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        CUDA_TRY(cudaMemcpy(kh.data(), kprev, n * sizeof(double), cudaMemcpyDeviceToHost));
+        cwx.assign(n, 0.0);
+        cwy.assign(n, 0.0);
+        cwz.assign(n, 0.0);
+        cDh.assign(n, 0.0);
+        const double h2 = s.h * s.h;
+        for (int l2 = 0; l2 < s.nz; ++l2)
+          for (int j = 0; j < s.ny; ++j)
+            for (int i = 0; i < s.nx; ++i) {
+              const int q = (l2 * s.ny + j) * s.nx + i;
+              double D = p.alpha * h2;
+              const double kc = kh[q];
+              auto face = [&](bool inside, int nb, int mult) {
+                return inside ? p.beta * (0.5 * (kc + kh[nb])) : mult * p.beta * kc;
+              };
+              D += face(i > 0, q - 1, bc_mult(p.bc[0])) + face(i < s.nx - 1, q + 1, bc_mult(p.bc[1]));
+              D += face(j > 0, q - s.nx, bc_mult(p.bc[2])) + face(j < s.ny - 1, q + s.nx, bc_mult(p.bc[3]));
+              if (p.dim == 3)
+                D += face(l2 > 0, q - s.nx * s.ny, bc_mult(p.bc[4])) +
+                     face(l2 < s.nz - 1, q + s.nx * s.ny, bc_mult(p.bc[5]));
+              if (i < s.nx - 1) cwx[q] = p.beta * (0.5 * (kc + kh[q + 1]));
+              if (j < s.ny - 1) cwy[q] = p.beta * (0.5 * (kc + kh[q + s.nx]));
+              if (p.dim == 3 && l2 < s.nz - 1) cwz[q] = p.beta * (0.5 * (kc + kh[q + s.nx * s.ny]));
+              cDh[q] = D / h2;
+            }
+      }
+    }
+  }
+  if (buffers) {
+    H.u.assign(c->nlev, nullptr);
+    H.f.assign(c->nlev, nullptr);
+    H.r.assign(c->nlev, nullptr);
+    H.u0.assign(c->nlev, nullptr);
+    for (int l = 0; l < c->nlev; ++l) {
+      const int64_t n = c->shape[l].cells();
+      STATUS_TRY(dev_alloc(H, &H.r[l], n));
+      if (l > 0 || level0_buffers) {
+        STATUS_TRY(dev_alloc(H, &H.u[l], n));
+        STATUS_TRY(dev_alloc(H, &H.f[l], n));
+      }
+      if (l > 0) STATUS_TRY(dev_alloc(H, &H.u0[l], n));
+    }
+    T** arrs[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 4; ++k) STATUS_TRY(dev_alloc(H, &arrs[k], kMaxLevels));
+    H.d_u = arrs[0];
+    H.d_f = arrs[1];
+    H.d_r = arrs[2];
+    H.d_u0 = arrs[3];
+    CUDA_TRY(cudaMemcpy(H.d_u, H.u.data(), c->nlev * sizeof(T*), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(H.d_f, H.f.data(), c->nlev * sizeof(T*), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(H.d_r, H.r.data(), c->nlev * sizeof(T*), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(H.d_u0, H.u0.data(), c->nlev * sizeof(T*), cudaMemcpyHostToDevice));
+    if (p.coarse_exact) {
+      std::vector<double> inv;
+      STATUS_TRY(coarse_inverse(c, c->shape[c->nlev - 1], cwx, cwy, cwz, cDh, inv));
+      std::vector<T> invT(inv.begin(), inv.end());
+      STATUS_TRY(dev_alloc(H, &H.cinv, (int64_t)invT.size()));
+      CUDA_TRY(cudaMemcpy(H.cinv, invT.data(), invT.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    H.allocated = true;
+  }
+  STATUS_TRY(dev_alloc(H, &H.d_desc, c->nlev));
+  CUDA_TRY(cudaMemcpy(H.d_desc, H.desc.data(), c->nlev * sizeof(LevelDesc<T>), cudaMemcpyHostToDevice));
+  return FAS_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// launches
+// ---------------------------------------------------------------------------------------------
+
+template <typename T, int DIM>
+void launch_smooth(fas_ctx* c, const LevelDesc<T>& L, T* u, const T* f, int sweeps) {
+  const int64_t half = (int64_t)(L.nx / 2) * L.ny * L.nz;
+  const int g = grid_for(c, half);
+  for (int s = 0; s < sweeps; ++s) {
+    k_smooth_colour<T, DIM><<<g, kBlock, 0, c->stream>>>(u, f, L, 1);
+    k_smooth_colour<T, DIM><<<g, kBlock, 0, c->stream>>>(u, f, L, 0);
+    c->launches += 2;
+  }
+}
+
+// ||f - A u||_2 into c->h_scalar[0] (after the stream sync); r (nullable) receives the residual.
+template <typename T, int DIM>
+void launch_residual(fas_ctx* c, const LevelDesc<T>& L, T* r, const T* u, const T* f, float nscale) {
+  const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+  const int g = grid_for(c, n);
+  k_residual<T, DIM><<<g, kBlock, 0, c->stream>>>(r, u, f, L, nscale, c->partials);
+  k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0 / nscale);
+  c->launches += 2;
+}
+
+template <typename T, int DIM>
+void vcycle_levels(fas_ctx* c, Hier<T>& H, T* utop, const T* ftop) {
+  const fas_params& p = c->p;
+  const int sw = H.switch_level;
+  for (int l = 0; l < sw; ++l) {
+    const LevelDesc<T>& L = H.desc[l];
+    T* u = l == 0 ? utop : H.u[l];
+    const T* f = l == 0 ? ftop : H.f[l];
+    launch_smooth<T, DIM>(c, L, u, f, p.nu1);
+    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+    k_residual<T, DIM><<<grid_for(c, n), kBlock, 0, c->stream>>>(H.r[l], u, f, L, 1.f, nullptr);
+    const int64_t nc = n >> DIM;
+    k_restrict<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.u[l + 1], H.u0[l + 1], H.f[l + 1], u, H.r[l],
+                                                                  L.nx, L.ny, L.nz);
+    k_tau<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.f[l + 1], H.u[l + 1], H.desc[l + 1]);
+    c->launches += 3;
+  }
+  CoarseArgs<T> A;
+  A.desc = H.d_desc;
+  A.u = H.d_u;
+  A.f = H.d_f;
+  A.r = H.d_r;
+  A.u0 = H.d_u0;
+  A.cinv = H.cinv;
+  A.l0 = sw;
+  A.nlev = H.nlev;
+  A.nu1 = p.nu1;
+  A.nu2 = p.nu2;
+  A.nuc = p.nu_coarse > 0 ? p.nu_coarse : p.nu1;
+  T* uc = sw == 0 ? utop : H.u[sw];
+  const T* fc = sw == 0 ? ftop : H.f[sw];
+  k_coarse_vcycle<T, DIM><<<1, kCoarseThreads, 0, c->stream>>>(A, uc, fc);
+  c->launches += 1;
+  for (int l = sw - 1; l >= 0; --l) {
+    const LevelDesc<T>& L = H.desc[l];
+    T* u = l == 0 ? utop : H.u[l];
+    const T* f = l == 0 ? ftop : H.f[l];
+    const int64_t nc = ((int64_t)L.nx * L.ny * L.nz) >> DIM;
+    k_prolong<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(u, H.u[l + 1], H.u0[l + 1], L.nx, L.ny, L.nz);
+    c->launches += 1;
+    launch_smooth<T, DIM>(c, L, u, f, p.nu2);
+  }
+}
+
+template <typename T>
+void vcycle(fas_ctx* c, Hier<T>& H, T* u, const T* f) {
+  if (c->p.dim == 2)
+    vcycle_levels<T, 2>(c, H, u, f);
+  else
+    vcycle_levels<T, 3>(c, H, u, f);
+}
+
+fas_status sync_read(fas_ctx* c, double* out) {
+  CUDA_TRY(cudaMemcpyAsync(c->h_scalar, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  CUDA_TRY(cudaGetLastError());
+  *out = c->h_scalar[0];
+  return FAS_OK;
+}
+
+// ||x||_2 of a float64 field of level-0 size (norm accumulated from float squares, scaled by nscale)
+fas_status norm_of(fas_ctx* c, const double* x, float nscale, double* out) {
+  const int64_t n = c->shape[0].cells();
+  const int g = grid_for(c, n);
+  k_norm2<double><<<g, kBlock, 0, c->stream>>>(x, n, nscale, c->partials);
+  k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0 / nscale);
+  c->launches += 2;
+  return sync_read(c, out);
+}
+
+float pick_scale(double norm, int64_t n) {
+  // power of two bringing the rms value near 1 so that float squares neither under- nor overflow
+  if (!(norm > 0.0) || !std::isfinite(norm)) return 1.f;
+  const double rms = norm / std::sqrt((double)n);
+  const int e = (int)std::lround(std::log2(rms));
+  return (float)std::ldexp(1.0, -std::max(-120, std::min(120, e)));
+}
+
+template <int DIM>
+fas_status residual64(fas_ctx* c, const double* u, const double* f, float nscale, double* out) {
+  launch_residual<double, DIM>(c, c->h64.desc[0], nullptr, u, f, nscale);
+  return sync_read(c, out);
+}
+
+fas_status residual_norm64(fas_ctx* c, const double* u, const double* f, float nscale, double* out) {
+  return c->p.dim == 2 ? residual64<2>(c, u, f, nscale, out) : residual64<3>(c, u, f, nscale, out);
+}
+
+// mixed: r32 = (float)(b - A u), returns ||b - A u||
+template <int DIM>
+fas_status ir_residual(fas_ctx* c, const double* u, const double* b, float nscale, double* out) {
+  const int64_t n = c->shape[0].cells();
+  const int g = grid_for(c, n);
+  k_ir_residual<DIM><<<g, kBlock, 0, c->stream>>>(c->h32.f[0], u, b, c->h64.desc[0], nscale, c->partials);
+  k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0 / nscale);
+  c->launches += 2;
+  return sync_read(c, out);
+}
+
+fas_status remove_mean(fas_ctx* c, double* x, const double* y) {
+  const int64_t n = c->shape[0].cells();
+  const int g = grid_for(c, n);
+  k_sum<double><<<g, kBlock, 0, c->stream>>>(y, n, c->partials);
+  k_finish_sum<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar + 1);
+  k_sub_mean<double><<<g, kBlock, 0, c->stream>>>(x, y, n, c->d_scalar + 1);
+  c->launches += 3;
+  CUDA_TRY(cudaGetLastError());
+  return FAS_OK;
+}
+
+double stop_value(const fas_ctx* c, double norm) {
+  if (c->p.tol_relative) return norm;
+  return std::pow(c->shape[0].h, c->p.dim / 2.0) * norm;  // Eq. residual: h^{d/2} ||r||_2
+}
+
+// One refinement step of the mixed solver: r32 holds b - A u on entry.
+fas_status mixed_step(fas_ctx* c, double* u) {
+  const int64_t n = c->shape[0].cells();
+  CUDA_TRY(cudaMemsetAsync(c->h32.u[0], 0, n * sizeof(float), c->stream));
+  const int inner = c->p.inner_cycles > 0 ? c->p.inner_cycles : 1;
+  for (int k = 0; k < inner; ++k) vcycle<float>(c, c->h32, c->h32.u[0], c->h32.f[0]);
+  k_ir_update<<<grid_for(c, n), kBlock, 0, c->stream>>>(u, c->h32.u[0], n);
+  c->launches += 1;
+  CUDA_TRY(cudaGetLastError());
+  return FAS_OK;
+}
+
+fas_status solve_impl(fas_ctx* c, double* u, const double* f_in, fas_info* info, int max_cycles) {
+  const fas_params& p = c->p;
+  const int64_t n = c->shape[0].cells();
+  const double* f = f_in;
+  if (c->singular) {
+    STATUS_TRY(remove_mean(c, c->fproj, f_in));
+    f = c->fproj;
+  }
+  double fn = 0.0;
+  STATUS_TRY(norm_of(c, f, 1.f, &fn));
+  const float ns = pick_scale(fn, n);
+  if (ns != 1.f) STATUS_TRY(norm_of(c, f, ns, &fn));
+  const bool mixed = p.precision == FAS_MIXED;
+  double rn = 0.0;
+  if (mixed) {
+    STATUS_TRY(p.dim == 2 ? ir_residual<2>(c, u, f, ns, &rn) : ir_residual<3>(c, u, f, ns, &rn));
+  } else {
+    STATUS_TRY(residual_norm64(c, u, f, ns, &rn));
+  }
+  fas_info loc;
+  std::memset(&loc, 0, sizeof(loc));
+  loc.res0 = stop_value(c, rn);
+  const double ref = p.tol_relative ? (fn > 0.0 ? fn : rn) : 1.0;
+  loc.res = loc.res0;
+  loc.rel = ref > 0.0 ? loc.res / ref : 0.0;
+  fas_status st = FAS_ENOTCONV;
+  for (int k = 0; k < max_cycles; ++k) {
+    if (mixed) {
+      STATUS_TRY(mixed_step(c, u));
+    } else {
+      vcycle<double>(c, c->h64, u, f);
+    }
+    if (c->singular) STATUS_TRY(remove_mean(c, u, u));
+    if (mixed) {
+      STATUS_TRY(p.dim == 2 ? ir_residual<2>(c, u, f, ns, &rn) : ir_residual<3>(c, u, f, ns, &rn));
+    } else {
+      STATUS_TRY(residual_norm64(c, u, f, ns, &rn));
+    }
+    loc.cycles++;
+    loc.res = stop_value(c, rn);
+    loc.rel = ref > 0.0 ? loc.res / ref : 0.0;
+    if (!std::isfinite(loc.res)) {
+      st = FAS_ENONFINITE;
+      break;
+    }
+    if (loc.res <= p.tol * ref) {
+      st = FAS_OK;
+      loc.converged = 1;
+      break;
+    }
+  }
+  loc.rho = (loc.cycles > 0 && loc.res0 > 0.0) ? std::pow(loc.res / loc.res0, 1.0 / loc.cycles) : 0.0;
+  if (info) *info = loc;
+  if (st == FAS_ENOTCONV && max_cycles == p.kmax)
+    return fail(st, "fas_solve: tolerance not reached within kmax cycles");
+  if (st == FAS_ENONFINITE) return fail(st, "fas_solve: residual is not finite");
+  return max_cycles == p.kmax ? st : FAS_OK;
+}
+
+fas_status check_ctx(const fas_ctx* c) {
+  if (!c) return fail(FAS_EINVAL, "null context");
+  return FAS_OK;
+}
+
+fas_status check_level(const fas_ctx* c, int level, bool needs_coarser) {
+  STATUS_TRY(check_ctx(c));
+  if (level < 0 || level >= c->nlev || (needs_coarser && level + 1 >= c->nlev))
+    return fail(FAS_EINVAL, "level out of range");
+  return FAS_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+
+extern "C" {
+
+void fas_default_params(fas_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->dim = 2;
+  p->n[0] = p->n[1] = p->n[2] = 64;
+  p->h = 1.0 / 64;
+  p->alpha = 1.0;
+  p->beta = 1.0;
+  p->kappa = nullptr;
+  p->kappa_const = 1.0;
+  for (int k = 0; k < 6; ++k) p->bc[k] = FAS_BC_NEUMANN;
+  p->nu1 = 2;
+  p->nu2 = 2;
+  p->nu_coarse = 0;
+  p->kmax = 20;
+  p->coarsest = 4;
+  p->coarse_exact = 0;
+  p->tol = 1e-10;
+  p->tol_relative = 1;
+  p->precision = FAS_FP64;
+  p->inner_cycles = 1;
+  p->use_graph = 1;
+}
+
+fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
+  if (!pin || !out) return fail(FAS_EINVAL, "fas_create: null argument");
+  *out = nullptr;
+  const fas_params& p = *pin;
+  if (p.dim != 2 && p.dim != 3) return fail(FAS_EINVAL, "dim must be 2 or 3");
+  for (int a = 0; a < p.dim; ++a)
+    if (!is_pow2(p.n[a]) || p.n[a] < 2) return fail(FAS_EINVAL, "every n must be a power of two >= 2");
+  if (!(p.h > 0.0) || !std::isfinite(p.h)) return fail(FAS_EINVAL, "h must be positive");
+  if (p.nu1 < 0 || p.nu2 < 0 || p.nu1 + p.nu2 < 1) return fail(FAS_EINVAL, "nu1, nu2 must be >= 0, sum >= 1");
+  if (p.kmax < 1) return fail(FAS_EINVAL, "kmax must be >= 1");
+  if (p.coarsest < 2 || !is_pow2(p.coarsest)) return fail(FAS_EINVAL, "coarsest must be a power of two >= 2");
+  if (!(p.tol >= 0.0)) return fail(FAS_EINVAL, "tol must be >= 0");
+  if (p.alpha < 0.0 || !(p.beta > 0.0)) return fail(FAS_EINVAL, "alpha must be >= 0 and beta > 0");
+  if (!p.kappa && !(p.kappa_const > 0.0)) return fail(FAS_EINVAL, "kappa_const must be positive");
+  if (p.precision != FAS_FP64 && p.precision != FAS_MIXED) return fail(FAS_EINVAL, "unknown precision");
+  for (int k = 0; k < 2 * p.dim; ++k)
+    if (p.bc[k] != FAS_BC_NEUMANN && p.bc[k] != FAS_BC_DIRICHLET) return fail(FAS_EINVAL, "unknown bc kind");
+
+  fas_ctx* c = new fas_ctx();
+  c->p = p;
+  if (c->p.dim == 2) c->p.n[2] = 1;
+  if (c->p.inner_cycles < 1) c->p.inner_cycles = 1;
+  c->stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  c->max_blocks = c->sm_count * 16;
+  bool all_neumann = true;
+  for (int k = 0; k < 2 * p.dim; ++k) all_neumann = all_neumann && p.bc[k] == FAS_BC_NEUMANN;
+  c->singular = p.alpha == 0.0 && all_neumann;
+  // levels: halve every axis while the shortest exceeds `coarsest`
+  LevelShape s{p.n[0], p.n[1], p.dim == 3 ? p.n[2] : 1, p.h};
+  c->shape.push_back(s);
+  auto shortest = [&](const LevelShape& q) { return p.dim == 3 ? std::min({q.nx, q.ny, q.nz}) : std::min(q.nx, q.ny); };
+  while (shortest(c->shape.back()) > p.coarsest && (int)c->shape.size() < kMaxLevels) {
+    LevelShape q = c->shape.back();
+    q.nx /= 2;
+    q.ny /= 2;
+    if (p.dim == 3) q.nz /= 2;
+    q.h *= 2.0;
+    c->shape.push_back(q);
+  }
+  c->nlev = (int)c->shape.size();
+  fas_status st = FAS_OK;
+  auto bail = [&](fas_status s2) {
+    fas_destroy(c);
+    return s2;
+  };
+  if (cudaMalloc(&c->partials, c->max_blocks * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "partials"));
+  if (cudaMalloc(&c->d_scalar, 8 * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "scalars"));
+  if (cudaMallocHost(&c->h_scalar, 8 * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "pinned"));
+  const bool mixed = p.precision == FAS_MIXED;
+  st = build_hier<double>(c, c->h64, !mixed, false);
+  if (st != FAS_OK) return bail(st);
+  if (mixed) {
+    st = build_hier<float>(c, c->h32, true, true);
+    if (st != FAS_OK) return bail(st);
+  }
+  if (c->singular && cudaMalloc(&c->fproj, s.cells() * sizeof(double)) != cudaSuccess)
+    return bail(fail(FAS_ENOMEM, "fproj"));
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return bail(fail(FAS_ECUDA, std::string("fas_create: ") + cudaGetErrorString(e)));
+  *out = c;
+  return FAS_OK;
+}
+
+fas_status fas_destroy(fas_ctx* c) {
+  if (!c) return FAS_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_hier(c->h64);
+  free_hier(c->h32);
+  if (c->partials) cudaFree(c->partials);
+  if (c->d_scalar) cudaFree(c->d_scalar);
+  if (c->h_scalar) cudaFreeHost(c->h_scalar);
+  if (c->b) cudaFree(c->b);
+  if (c->fproj) cudaFree(c->fproj);
+  delete c;
+  return FAS_OK;
+}
+
+int fas_num_levels(const fas_ctx* c) { return c ? c->nlev : 0; }
+
+fas_status fas_vcycle(fas_ctx* c, double* u, const double* f, fas_info* info) {
+  STATUS_TRY(check_ctx(c));
+  if (!u || !f) return fail(FAS_EINVAL, "fas_vcycle: null field");
+  return solve_impl(c, u, f, info, 1);
+}
+
+fas_status fas_solve(fas_ctx* c, double* u, const double* f, fas_info* info) {
+  STATUS_TRY(check_ctx(c));
+  if (!u || !f) return fail(FAS_EINVAL, "fas_solve: null field");
+  return solve_impl(c, u, f, info, c->p.kmax);
+}
+
+fas_status fas_heat_run(fas_ctx* c, double* u, const double* fsrc, double dt, int nsteps, fas_info* infos) {
+  STATUS_TRY(check_ctx(c));
+  if (!u || nsteps < 0) return fail(FAS_EINVAL, "fas_heat_run: bad argument");
+  if (c->p.alpha != 1.0 || std::fabs(c->p.beta - dt) > 1e-15 * std::fabs(dt))
+    return fail(FAS_EINVAL, "fas_heat_run: context must have alpha = 1 and beta = dt");
+  const int64_t n = c->shape[0].cells();
+  if (!c->b) CUDA_TRY(cudaMalloc(&c->b, n * sizeof(double)));
+  fas_status worst = FAS_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    k_heat_rhs<<<grid_for(c, n), kBlock, 0, c->stream>>>(c->b, u, fsrc, dt, n);
+    c->launches += 1;
+    fas_info inf;
+    fas_status st = solve_impl(c, u, c->b, &inf, c->p.kmax);
+    if (infos) infos[s] = inf;
+    if (st != FAS_OK && st != FAS_ENOTCONV) return st;
+    if (st == FAS_ENOTCONV) worst = st;
+  }
+  return worst;
+}
+
+fas_status fas_heat_run_host(fas_ctx* c, double* u_host, const double* fsrc_host, double dt, int nsteps,
+                             fas_info* infos) {
+  STATUS_TRY(check_ctx(c));
+  if (!u_host) return fail(FAS_EINVAL, "fas_heat_run_host: null u");
+  const int64_t n = c->shape[0].cells();
+  double *du = nullptr, *df = nullptr;
+  CUDA_TRY(cudaMalloc(&du, n * sizeof(double)));
+  if (fsrc_host && cudaMalloc(&df, n * sizeof(double)) != cudaSuccess) {
+    cudaFree(du);
+    return fail(FAS_ENOMEM, "fas_heat_run_host: device buffers");
+  }
+  cudaMemcpyAsync(du, u_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  if (df) cudaMemcpyAsync(df, fsrc_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  fas_status st = fas_heat_run(c, du, df, dt, nsteps, infos);
+  cudaMemcpyAsync(u_host, du, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  cudaFree(du);
+  if (df) cudaFree(df);
+  if (e != cudaSuccess) return fail(FAS_ECUDA, cudaGetErrorString(e));
+  return st;
+}
+
+fas_status fas_residual(fas_ctx* c, int level, const double* u, const double* f, double* out, double* norm2) {
+  STATUS_TRY(check_level(c, level, false));
+  const LevelDesc<double>& L = c->h64.desc[level];
+  if (c->p.dim == 2)
+    launch_residual<double, 2>(c, L, out, u, f, 1.f);
+  else
+    launch_residual<double, 3>(c, L, out, u, f, 1.f);
+  double v = 0.0;
+  STATUS_TRY(sync_read(c, &v));
+  if (norm2) *norm2 = v;
+  return FAS_OK;
+}
+
+fas_status fas_smooth(fas_ctx* c, int level, double* u, const double* f, int sweeps) {
+  STATUS_TRY(check_level(c, level, false));
+  if (sweeps < 0) return fail(FAS_EINVAL, "sweeps must be >= 0");
+  const LevelDesc<double>& L = c->h64.desc[level];
+  if (c->p.dim == 2)
+    launch_smooth<double, 2>(c, L, u, f, sweeps);
+  else
+    launch_smooth<double, 3>(c, L, u, f, sweeps);
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  CUDA_TRY(cudaGetLastError());
+  return FAS_OK;
+}
+
+fas_status fas_restrict(fas_ctx* c, int level, const double* u, double* uc) {
+  STATUS_TRY(check_level(c, level, true));
+  const LevelShape& s = c->shape[level];
+  const int64_t nc = s.cells() >> c->p.dim;
+  if (c->p.dim == 2)
+    k_restrict<double, 2><<<grid_for(c, nc), kBlock, 0, c->stream>>>(uc, nullptr, nullptr, u, nullptr, s.nx, s.ny, s.nz);
+  else
+    k_restrict<double, 3><<<grid_for(c, nc), kBlock, 0, c->stream>>>(uc, nullptr, nullptr, u, nullptr, s.nx, s.ny, s.nz);
+  c->launches += 1;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  CUDA_TRY(cudaGetLastError());
+  return FAS_OK;
+}
+
+fas_status fas_prolong_add(fas_ctx* c, int level, double* u, const double* cc) {
+  STATUS_TRY(check_level(c, level, true));
+  const LevelShape& s = c->shape[level];
+  const int64_t nc = s.cells() >> c->p.dim;
+  if (c->p.dim == 2)
+    k_prolong<double, 2><<<grid_for(c, nc), kBlock, 0, c->stream>>>(u, cc, nullptr, s.nx, s.ny, s.nz);
+  else
+    k_prolong<double, 3><<<grid_for(c, nc), kBlock, 0, c->stream>>>(u, cc, nullptr, s.nx, s.ny, s.nz);
+  c->launches += 1;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  CUDA_TRY(cudaGetLastError());
+  return FAS_OK;
+}
+
+const char* fas_last_error(void) { return g_last_error.c_str(); }
+
+long long fas_launch_count(const fas_ctx* c, int reset) {
+  if (!c) return 0;
+  long long v = c->launches;
+  if (reset) const_cast<fas_ctx*>(c)->launches = 0;
+  return v;
+}
+
+}  // extern "C"

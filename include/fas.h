@@ -68,6 +68,9 @@ typedef struct {
   int precision;         /* fas_precision: FP64, or FP32 inner cycles in FP64 refinement        */
   int inner_cycles;      /* FAS_MIXED: FP32 V-cycles per refinement step (default 1)          */
   int use_graph;         /* 1: capture repeated launch sequences in CUDA graphs (default 1)     */
+  int path;              /* 0: sweep-fused kernels where the level allows (default);
+                          * 1: one kernel per operation everywhere (reference path)           */
+  int seg_rows;          /* rows per warp segment in the fused 2D kernels (0: default 128)      */
 } fas_params;
 
 /* Per-solve report. res0/res are ||f - A u||_2 before the first and after the last cycle
@@ -130,6 +133,37 @@ fas_status fas_restrict(fas_ctx* ctx, int level, const double* u, double* uc);
 
 /* u += P(c) (Appendix C piecewise-constant prolongation), c of level + 1, u of level `level`. */
 fas_status fas_prolong_add(fas_ctx* ctx, int level, double* u, const double* c);
+
+/* --- kernel timing (CUDA events on the context's stream) ------------------------------------ */
+
+/* Kernel families for fas_prof_read. */
+typedef enum {
+  FAS_K_SMOOTH = 0,      /* X-MCGS sweeps (colour phases or fused sweeps)                       */
+  FAS_K_RESIDUAL = 1,    /* residual (+ restriction + tau correction when fused)                */
+  FAS_K_RESTRICT = 2,    /* restriction of u and r                                              */
+  FAS_K_TAU = 3,         /* coarse source term f_c = R(r) + A_c R(u)                             */
+  FAS_K_PROLONG = 4,     /* prolongation of the correction (+ post-smoothing when fused)         */
+  FAS_K_COARSE = 5,      /* single-CTA V-cycle over the small levels                             */
+  FAS_K_IR = 6,          /* mixed precision: float64 update and residual                         */
+  FAS_K_NORM = 7,        /* norms and means                                                     */
+  FAS_K_OTHER = 8,       /* right-hand sides, fills, conversions                                */
+  FAS_K_NFAMILIES = 9
+} fas_kernel_family;
+
+/* Per (family, level) totals since the last fas_prof_enable(ctx, 1). */
+typedef struct {
+  int family, level;
+  long long launches;
+  double ms;             /* sum of CUDA-event durations of the launches                        */
+  double units;          /* cells of that level processed by the launches (per launch summed)   */
+} fas_prof_record;
+
+/* Start (on != 0: clears previous records) or stop recording an event pair around every launch. */
+fas_status fas_prof_enable(fas_ctx* ctx, int on);
+
+/* Synchronise the stream and write up to `cap` aggregated records; *count receives the number of
+ * (family, level) pairs seen (may exceed cap). */
+fas_status fas_prof_read(fas_ctx* ctx, fas_prof_record* out, int cap, int* count);
 
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char* fas_last_error(void);

@@ -22,6 +22,7 @@ __all__ = [
     "FasError", "fas_params", "fas_info", "load", "fas_default_params", "fas_create", "fas_destroy",
     "fas_num_levels", "fas_vcycle", "fas_solve", "fas_heat_run", "fas_heat_run_host", "fas_residual",
     "fas_smooth", "fas_restrict", "fas_prolong_add", "fas_last_error", "fas_launch_count", "Solver",
+    "fas_prof_enable", "fas_prof_read", "make_params",
 ]
 
 FAS_OK, FAS_EINVAL, FAS_ENOMEM, FAS_ENOTCONV, FAS_ENONFINITE, FAS_ETIMEOUT, FAS_ECUDA, FAS_EUNSUPPORTED = range(8)
@@ -39,7 +40,7 @@ class fas_params(ctypes.Structure):
         ("nu2", ctypes.c_int), ("nu_coarse", ctypes.c_int), ("kmax", ctypes.c_int),
         ("coarsest", ctypes.c_int), ("coarse_exact", ctypes.c_int), ("tol", ctypes.c_double),
         ("tol_relative", ctypes.c_int), ("precision", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-        ("use_graph", ctypes.c_int),
+        ("use_graph", ctypes.c_int), ("path", ctypes.c_int), ("seg_rows", ctypes.c_int),
     ]
 
 
@@ -88,6 +89,8 @@ def load(path: str | None = None):
         "fas_prolong_add": (_I, [_P, _I, _P, _P]),
         "fas_last_error": (ctypes.c_char_p, []),
         "fas_launch_count": (ctypes.c_longlong, [_P, _I]),
+        "fas_prof_enable": (_I, [_P, _I]),
+        "fas_prof_read": (_I, [_P, ctypes.c_void_p, _I, ctypes.POINTER(_I)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -243,6 +246,32 @@ def fas_prolong_add(ctx: _Ctx, level: int, u, c) -> None:
 
 def fas_launch_count(ctx: _Ctx, reset: bool = False) -> int:
     return load().fas_launch_count(ctx.handle, 1 if reset else 0)
+
+
+class fas_prof_record(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int), ("level", ctypes.c_int), ("launches", ctypes.c_longlong),
+                ("ms", ctypes.c_double), ("units", ctypes.c_double)]
+
+
+FAMILIES = ["smooth", "residual", "restrict", "tau", "prolong", "coarse", "ir", "norm", "other"]
+
+
+def fas_prof_enable(ctx: _Ctx, on: bool = True) -> None:
+    _check(load().fas_prof_enable(ctx.handle, 1 if on else 0), "fas_prof_enable")
+
+
+def fas_prof_read(ctx: _Ctx):
+    """Aggregated kernel timings: list of dicts (family, level, launches, ms, units)."""
+    cap = 256
+    buf = (fas_prof_record * cap)()
+    cnt = _I()
+    _check(load().fas_prof_read(ctx.handle, buf, cap, ctypes.byref(cnt)), "fas_prof_read")
+    out = []
+    for k in range(min(cnt.value, cap)):
+        r = buf[k]
+        out.append(dict(family=FAMILIES[r.family] if 0 <= r.family < len(FAMILIES) else r.family,
+                        level=r.level, launches=r.launches, ms=r.ms, units=r.units))
+    return out
 
 
 def make_params(shape, h, alpha=1.0, beta=1.0, kappa_const=1.0, bc=None, **kw) -> fas_params:

@@ -21,6 +21,8 @@ struct Hier {
   std::vector<LevelDesc<T>> desc;
   LevelDesc<T>* d_desc = nullptr;
   std::vector<T*> u, f, r, u0;
+  std::vector<T*> u2, rc;  // fused path: second u buffer (ping-pong) and R(r) from the finer level
+  int nfast = 0;           // levels 0..nfast-1 use the fused kernels
   T** d_u = nullptr;
   T** d_f = nullptr;
   T** d_r = nullptr;
@@ -38,6 +40,12 @@ struct LevelShape {
 
 }  // namespace fasmg
 
+struct ProfSpan {
+  cudaEvent_t beg, end;
+  int family, level;
+  double units;
+};
+
 struct fas_ctx {
   fas_params p;
   cudaStream_t stream = nullptr;
@@ -54,4 +62,9 @@ struct fas_ctx {
   double* b = nullptr;         // heat-step right-hand side (fine, float64)
   double* fproj = nullptr;     // mean-free copy of f for singular problems
   long long launches = 0;
+  // kernel timing
+  bool prof = false;
+  std::vector<ProfSpan> spans;
+  std::vector<cudaEvent_t> event_pool;
+  size_t pool_next = 0;
 };

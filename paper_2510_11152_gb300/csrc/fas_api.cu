@@ -15,6 +15,7 @@
 
 #include "basic_kernels.cuh"
 #include "context.h"
+#include "stream2d.h"
 
 using namespace fasmg;
 
@@ -51,6 +52,41 @@ int grid_for(const fas_ctx* c, int64_t work) {
   int64_t g = (work + kBlock - 1) / kBlock;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, c->max_blocks));
 }
+
+// ---------------------------------------------------------------------------------------------
+// kernel timing: an event pair around each launch while recording is on
+// ---------------------------------------------------------------------------------------------
+
+cudaEvent_t pool_event(fas_ctx* c) {
+  if (c->pool_next == c->event_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->event_pool.push_back(e);
+  }
+  return c->event_pool[c->pool_next++];
+}
+
+struct Prof {
+  fas_ctx* c;
+  ProfSpan span;
+  bool on;
+  Prof(fas_ctx* ctx, int family, int level, double units) : c(ctx), on(ctx->prof) {
+    c->launches += 1;
+    if (!on) return;
+    span.beg = pool_event(c);
+    span.end = pool_event(c);
+    span.family = family;
+    span.level = level;
+    span.units = units;
+    on = span.beg && span.end;
+    if (on) cudaEventRecord(span.beg, c->stream);
+  }
+  ~Prof() {
+    if (!on) return;
+    cudaEventRecord(span.end, c->stream);
+    c->spans.push_back(span);
+  }
+};
 
 // ---------------------------------------------------------------------------------------------
 // level descriptors
@@ -105,6 +141,9 @@ void free_hier(Hier<T>& H) {
   H.f.clear();
   H.r.clear();
   H.u0.clear();
+  H.u2.clear();
+  H.rc.clear();
+  H.nfast = 0;
   H.d_desc = nullptr;
   H.cinv = nullptr;
   H.allocated = false;
@@ -277,6 +316,20 @@ fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers)
       }
       if (l > 0) STATUS_TRY(dev_alloc(H, &H.u0[l], n));
     }
+    // sweep-fused 2D path (float32 only): consecutive levels from the finest that the fused kernels
+    // handle and that are larger than the single-CTA switch level
+    H.nfast = 0;
+    if (sizeof(T) == 4 && p.dim == 2 && p.path == 0 && !p.kappa && p.nu1 >= 1 && p.nu2 >= 1) {
+      while (H.nfast < H.switch_level &&
+             stream2d_supported(c->shape[H.nfast].nx, c->shape[H.nfast].ny, std::max(p.nu1, p.nu2)))
+        H.nfast++;
+    }
+    H.u2.assign(c->nlev, nullptr);
+    H.rc.assign(c->nlev, nullptr);
+    for (int l = 0; l < H.nfast; ++l) {
+      STATUS_TRY(dev_alloc(H, &H.u2[l], c->shape[l].cells()));
+      if (l + 1 < H.nfast) STATUS_TRY(dev_alloc(H, &H.rc[l + 1], c->shape[l + 1].cells()));
+    }
     T** arrs[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int k = 0; k < 4; ++k) STATUS_TRY(dev_alloc(H, &arrs[k], kMaxLevels));
     H.d_u = arrs[0];
@@ -306,43 +359,37 @@ fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers)
 // ---------------------------------------------------------------------------------------------
 
 template <typename T, int DIM>
-void launch_smooth(fas_ctx* c, const LevelDesc<T>& L, T* u, const T* f, int sweeps) {
+void launch_smooth(fas_ctx* c, const LevelDesc<T>& L, int level, T* u, const T* f, int sweeps) {
   const int64_t half = (int64_t)(L.nx / 2) * L.ny * L.nz;
   const int g = grid_for(c, half);
   for (int s = 0; s < sweeps; ++s) {
-    k_smooth_colour<T, DIM><<<g, kBlock, 0, c->stream>>>(u, f, L, 1);
-    k_smooth_colour<T, DIM><<<g, kBlock, 0, c->stream>>>(u, f, L, 0);
-    c->launches += 2;
+    {
+      Prof pr(c, FAS_K_SMOOTH, level, (double)half);
+      k_smooth_colour<T, DIM><<<g, kBlock, 0, c->stream>>>(u, f, L, 1);
+    }
+    {
+      Prof pr(c, FAS_K_SMOOTH, level, (double)half);
+      k_smooth_colour<T, DIM><<<g, kBlock, 0, c->stream>>>(u, f, L, 0);
+    }
   }
 }
 
-// ||f - A u||_2 into c->h_scalar[0] (after the stream sync); r (nullable) receives the residual.
+// ||f - A u||_2 into c->d_scalar[0]; r (nullable) receives the residual.
 template <typename T, int DIM>
-void launch_residual(fas_ctx* c, const LevelDesc<T>& L, T* r, const T* u, const T* f, float nscale) {
+void launch_residual(fas_ctx* c, const LevelDesc<T>& L, int level, T* r, const T* u, const T* f, float nscale) {
   const int64_t n = (int64_t)L.nx * L.ny * L.nz;
   const int g = grid_for(c, n);
-  k_residual<T, DIM><<<g, kBlock, 0, c->stream>>>(r, u, f, L, nscale, c->partials);
+  {
+    Prof pr(c, FAS_K_RESIDUAL, level, (double)n);
+    k_residual<T, DIM><<<g, kBlock, 0, c->stream>>>(r, u, f, L, nscale, c->partials);
+  }
+  Prof pr(c, FAS_K_NORM, level, 0.0);
   k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0 / nscale);
-  c->launches += 2;
 }
 
 template <typename T, int DIM>
-void vcycle_levels(fas_ctx* c, Hier<T>& H, T* utop, const T* ftop) {
+void launch_coarse(fas_ctx* c, Hier<T>& H, int l0, T* utop, const T* ftop) {
   const fas_params& p = c->p;
-  const int sw = H.switch_level;
-  for (int l = 0; l < sw; ++l) {
-    const LevelDesc<T>& L = H.desc[l];
-    T* u = l == 0 ? utop : H.u[l];
-    const T* f = l == 0 ? ftop : H.f[l];
-    launch_smooth<T, DIM>(c, L, u, f, p.nu1);
-    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
-    k_residual<T, DIM><<<grid_for(c, n), kBlock, 0, c->stream>>>(H.r[l], u, f, L, 1.f, nullptr);
-    const int64_t nc = n >> DIM;
-    k_restrict<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.u[l + 1], H.u0[l + 1], H.f[l + 1], u, H.r[l],
-                                                                  L.nx, L.ny, L.nz);
-    k_tau<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.f[l + 1], H.u[l + 1], H.desc[l + 1]);
-    c->launches += 3;
-  }
   CoarseArgs<T> A;
   A.desc = H.d_desc;
   A.u = H.d_u;
@@ -350,32 +397,99 @@ void vcycle_levels(fas_ctx* c, Hier<T>& H, T* utop, const T* ftop) {
   A.r = H.d_r;
   A.u0 = H.d_u0;
   A.cinv = H.cinv;
-  A.l0 = sw;
+  A.l0 = l0;
   A.nlev = H.nlev;
   A.nu1 = p.nu1;
   A.nu2 = p.nu2;
   A.nuc = p.nu_coarse > 0 ? p.nu_coarse : p.nu1;
-  T* uc = sw == 0 ? utop : H.u[sw];
-  const T* fc = sw == 0 ? ftop : H.f[sw];
-  k_coarse_vcycle<T, DIM><<<1, kCoarseThreads, 0, c->stream>>>(A, uc, fc);
-  c->launches += 1;
+  Prof pr(c, FAS_K_COARSE, l0, (double)c->shape[l0].cells());
+  k_coarse_vcycle<T, DIM><<<1, kCoarseThreads, 0, c->stream>>>(A, utop, ftop);
+}
+
+// One V-cycle through the per-operation kernels (any value type, 2D or 3D).
+template <typename T, int DIM>
+void vcycle_basic(fas_ctx* c, Hier<T>& H, T* utop, const T* ftop) {
+  const fas_params& p = c->p;
+  const int sw = H.switch_level;
+  for (int l = 0; l < sw; ++l) {
+    const LevelDesc<T>& L = H.desc[l];
+    T* u = l == 0 ? utop : H.u[l];
+    const T* f = l == 0 ? ftop : H.f[l];
+    launch_smooth<T, DIM>(c, L, l, u, f, p.nu1);
+    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+    {
+      Prof pr(c, FAS_K_RESIDUAL, l, (double)n);
+      k_residual<T, DIM><<<grid_for(c, n), kBlock, 0, c->stream>>>(H.r[l], u, f, L, 1.f, nullptr);
+    }
+    const int64_t nc = n >> DIM;
+    {
+      Prof pr(c, FAS_K_RESTRICT, l, (double)n);
+      k_restrict<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.u[l + 1], H.u0[l + 1], H.f[l + 1], u,
+                                                                    H.r[l], L.nx, L.ny, L.nz);
+    }
+    {
+      Prof pr(c, FAS_K_TAU, l + 1, (double)nc);
+      k_tau<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.f[l + 1], H.u[l + 1], H.desc[l + 1]);
+    }
+  }
+  launch_coarse<T, DIM>(c, H, sw, sw == 0 ? utop : H.u[sw], sw == 0 ? ftop : H.f[sw]);
   for (int l = sw - 1; l >= 0; --l) {
     const LevelDesc<T>& L = H.desc[l];
     T* u = l == 0 ? utop : H.u[l];
     const T* f = l == 0 ? ftop : H.f[l];
-    const int64_t nc = ((int64_t)L.nx * L.ny * L.nz) >> DIM;
-    k_prolong<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(u, H.u[l + 1], H.u0[l + 1], L.nx, L.ny, L.nz);
-    c->launches += 1;
-    launch_smooth<T, DIM>(c, L, u, f, p.nu2);
+    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+    {
+      Prof pr(c, FAS_K_PROLONG, l, (double)n);
+      k_prolong<T, DIM><<<grid_for(c, n >> DIM), kBlock, 0, c->stream>>>(u, H.u[l + 1], H.u0[l + 1], L.nx, L.ny,
+                                                                         L.nz);
+    }
+    launch_smooth<T, DIM>(c, L, l, u, f, p.nu2);
   }
+}
+
+// rows per warp segment of the fused kernels: a multiple of 8 (row pairs stay aligned)
+int seg_rows(const fas_ctx* c) {
+  const int s = c->p.seg_rows > 0 ? c->p.seg_rows : 128;
+  return std::max(8, (s + 7) / 8 * 8);
+}
+
+// One float32 V-cycle through the sweep-fused 2D kernels on levels 0..nfast-1 (ping-pong buffers u/u2,
+// R(r) in rc), the per-operation tau kernel and the single-CTA kernel below. Result in H.u[0].
+// zero_init: the level-0 initial guess is 0 (H.u[0] is not read).
+fas_status vcycle_fast(fas_ctx* c, Hier<float>& H, bool zero_init) {
+  const fas_params& p = c->p;
+  const int nf = H.nfast;
+  const int seg = seg_rows(c);
+  for (int l = 0; l < nf; ++l) {
+    const LevelDesc<float>& L = H.desc[l];
+    const bool tau = l > 0;
+    float* rc_next = (l + 1 == nf) ? H.f[l + 1] : H.rc[l + 1];
+    Prof pr(c, FAS_K_SMOOTH, l, (double)c->shape[l].cells());
+    cudaError_t e = launch_stream2d_pre(H.u[l], tau ? H.rc[l] : H.f[l], tau ? H.f[l] : nullptr, H.u2[l], H.u[l + 1],
+                                        rc_next, L, p.nu1, l == 0 && zero_init, tau, seg, c->stream);
+    if (e != cudaSuccess) return fail(FAS_ECUDA, std::string("stream2d pre: ") + cudaGetErrorString(e));
+  }
+  {
+    const int64_t nc = c->shape[nf].cells();
+    Prof pr(c, FAS_K_TAU, nf, (double)nc);
+    k_tau<float, 2><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.f[nf], H.u[nf], H.desc[nf]);
+  }
+  launch_coarse<float, 2>(c, H, nf, H.u[nf], H.f[nf]);
+  for (int l = nf - 1; l >= 0; --l) {
+    const LevelDesc<float>& L = H.desc[l];
+    Prof pr(c, FAS_K_PROLONG, l, (double)c->shape[l].cells());
+    cudaError_t e = launch_stream2d_post(H.u2[l], H.f[l], H.u[l + 1], H.u[l], L, p.nu2, seg, c->stream);
+    if (e != cudaSuccess) return fail(FAS_ECUDA, std::string("stream2d post: ") + cudaGetErrorString(e));
+  }
+  return FAS_OK;
 }
 
 template <typename T>
 void vcycle(fas_ctx* c, Hier<T>& H, T* u, const T* f) {
   if (c->p.dim == 2)
-    vcycle_levels<T, 2>(c, H, u, f);
+    vcycle_basic<T, 2>(c, H, u, f);
   else
-    vcycle_levels<T, 3>(c, H, u, f);
+    vcycle_basic<T, 3>(c, H, u, f);
 }
 
 fas_status sync_read(fas_ctx* c, double* out) {
@@ -386,13 +500,18 @@ fas_status sync_read(fas_ctx* c, double* out) {
   return FAS_OK;
 }
 
-// ||x||_2 of a float64 field of level-0 size (norm accumulated from float squares, scaled by nscale)
+// ||x||_2 of a float64 field of level-0 size (squares of the float-rounded values, scaled by nscale)
 fas_status norm_of(fas_ctx* c, const double* x, float nscale, double* out) {
   const int64_t n = c->shape[0].cells();
   const int g = grid_for(c, n);
-  k_norm2<double><<<g, kBlock, 0, c->stream>>>(x, n, nscale, c->partials);
-  k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0 / nscale);
-  c->launches += 2;
+  {
+    Prof pr(c, FAS_K_NORM, 0, (double)n);
+    k_norm2<double><<<g, kBlock, 0, c->stream>>>(x, n, nscale, c->partials);
+  }
+  {
+    Prof pr(c, FAS_K_NORM, 0, 0.0);
+    k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0 / nscale);
+  }
   return sync_read(c, out);
 }
 
@@ -406,7 +525,7 @@ float pick_scale(double norm, int64_t n) {
 
 template <int DIM>
 fas_status residual64(fas_ctx* c, const double* u, const double* f, float nscale, double* out) {
-  launch_residual<double, DIM>(c, c->h64.desc[0], nullptr, u, f, nscale);
+  launch_residual<double, DIM>(c, c->h64.desc[0], 0, nullptr, u, f, nscale);
   return sync_read(c, out);
 }
 
@@ -419,19 +538,32 @@ template <int DIM>
 fas_status ir_residual(fas_ctx* c, const double* u, const double* b, float nscale, double* out) {
   const int64_t n = c->shape[0].cells();
   const int g = grid_for(c, n);
-  k_ir_residual<DIM><<<g, kBlock, 0, c->stream>>>(c->h32.f[0], u, b, c->h64.desc[0], nscale, c->partials);
-  k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0 / nscale);
-  c->launches += 2;
+  {
+    Prof pr(c, FAS_K_IR, 0, (double)n);
+    k_ir_residual<DIM><<<g, kBlock, 0, c->stream>>>(c->h32.f[0], u, b, c->h64.desc[0], nscale, c->partials);
+  }
+  {
+    Prof pr(c, FAS_K_NORM, 0, 0.0);
+    k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0 / nscale);
+  }
   return sync_read(c, out);
 }
 
 fas_status remove_mean(fas_ctx* c, double* x, const double* y) {
   const int64_t n = c->shape[0].cells();
   const int g = grid_for(c, n);
-  k_sum<double><<<g, kBlock, 0, c->stream>>>(y, n, c->partials);
-  k_finish_sum<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar + 1);
-  k_sub_mean<double><<<g, kBlock, 0, c->stream>>>(x, y, n, c->d_scalar + 1);
-  c->launches += 3;
+  {
+    Prof pr(c, FAS_K_NORM, 0, (double)n);
+    k_sum<double><<<g, kBlock, 0, c->stream>>>(y, n, c->partials);
+  }
+  {
+    Prof pr(c, FAS_K_NORM, 0, 0.0);
+    k_finish_sum<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar + 1);
+  }
+  {
+    Prof pr(c, FAS_K_OTHER, 0, (double)n);
+    k_sub_mean<double><<<g, kBlock, 0, c->stream>>>(x, y, n, c->d_scalar + 1);
+  }
   CUDA_TRY(cudaGetLastError());
   return FAS_OK;
 }
@@ -441,14 +573,22 @@ double stop_value(const fas_ctx* c, double norm) {
   return std::pow(c->shape[0].h, c->p.dim / 2.0) * norm;  // Eq. residual: h^{d/2} ||r||_2
 }
 
-// One refinement step of the mixed solver: r32 holds b - A u on entry.
+// One refinement step of the mixed solver: r32 (h32.f[0]) holds b - A u on entry; float32 V-cycles on
+// A e = r32 from e = 0, then u += e in float64.
 fas_status mixed_step(fas_ctx* c, double* u) {
   const int64_t n = c->shape[0].cells();
-  CUDA_TRY(cudaMemsetAsync(c->h32.u[0], 0, n * sizeof(float), c->stream));
   const int inner = c->p.inner_cycles > 0 ? c->p.inner_cycles : 1;
-  for (int k = 0; k < inner; ++k) vcycle<float>(c, c->h32, c->h32.u[0], c->h32.f[0]);
-  k_ir_update<<<grid_for(c, n), kBlock, 0, c->stream>>>(u, c->h32.u[0], n);
-  c->launches += 1;
+  Hier<float>& H = c->h32;
+  if (H.nfast > 0) {
+    for (int k = 0; k < inner; ++k) STATUS_TRY(vcycle_fast(c, H, k == 0));
+  } else {
+    CUDA_TRY(cudaMemsetAsync(H.u[0], 0, n * sizeof(float), c->stream));
+    for (int k = 0; k < inner; ++k) vcycle<float>(c, H, H.u[0], H.f[0]);
+  }
+  {
+    Prof pr(c, FAS_K_IR, 0, (double)n);
+    k_ir_update<<<grid_for(c, n), kBlock, 0, c->stream>>>(u, H.u[0], n);
+  }
   CUDA_TRY(cudaGetLastError());
   return FAS_OK;
 }
@@ -554,6 +694,8 @@ void fas_default_params(fas_params* p) {
   p->precision = FAS_FP64;
   p->inner_cycles = 1;
   p->use_graph = 1;
+  p->path = 0;
+  p->seg_rows = 0;
 }
 
 fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
@@ -632,6 +774,7 @@ fas_status fas_destroy(fas_ctx* c) {
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
   if (c->b) cudaFree(c->b);
   if (c->fproj) cudaFree(c->fproj);
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   delete c;
   return FAS_OK;
 }
@@ -659,8 +802,10 @@ fas_status fas_heat_run(fas_ctx* c, double* u, const double* fsrc, double dt, in
   if (!c->b) CUDA_TRY(cudaMalloc(&c->b, n * sizeof(double)));
   fas_status worst = FAS_OK;
   for (int s = 0; s < nsteps; ++s) {
-    k_heat_rhs<<<grid_for(c, n), kBlock, 0, c->stream>>>(c->b, u, fsrc, dt, n);
-    c->launches += 1;
+    {
+      Prof pr(c, FAS_K_OTHER, 0, (double)n);
+      k_heat_rhs<<<grid_for(c, n), kBlock, 0, c->stream>>>(c->b, u, fsrc, dt, n);
+    }
     fas_info inf;
     fas_status st = solve_impl(c, u, c->b, &inf, c->p.kmax);
     if (infos) infos[s] = inf;
@@ -696,9 +841,9 @@ fas_status fas_residual(fas_ctx* c, int level, const double* u, const double* f,
   STATUS_TRY(check_level(c, level, false));
   const LevelDesc<double>& L = c->h64.desc[level];
   if (c->p.dim == 2)
-    launch_residual<double, 2>(c, L, out, u, f, 1.f);
+    launch_residual<double, 2>(c, L, level, out, u, f, 1.f);
   else
-    launch_residual<double, 3>(c, L, out, u, f, 1.f);
+    launch_residual<double, 3>(c, L, level, out, u, f, 1.f);
   double v = 0.0;
   STATUS_TRY(sync_read(c, &v));
   if (norm2) *norm2 = v;
@@ -710,9 +855,9 @@ fas_status fas_smooth(fas_ctx* c, int level, double* u, const double* f, int swe
   if (sweeps < 0) return fail(FAS_EINVAL, "sweeps must be >= 0");
   const LevelDesc<double>& L = c->h64.desc[level];
   if (c->p.dim == 2)
-    launch_smooth<double, 2>(c, L, u, f, sweeps);
+    launch_smooth<double, 2>(c, L, level, u, f, sweeps);
   else
-    launch_smooth<double, 3>(c, L, u, f, sweeps);
+    launch_smooth<double, 3>(c, L, level, u, f, sweeps);
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   CUDA_TRY(cudaGetLastError());
   return FAS_OK;
@@ -722,11 +867,13 @@ fas_status fas_restrict(fas_ctx* c, int level, const double* u, double* uc) {
   STATUS_TRY(check_level(c, level, true));
   const LevelShape& s = c->shape[level];
   const int64_t nc = s.cells() >> c->p.dim;
-  if (c->p.dim == 2)
-    k_restrict<double, 2><<<grid_for(c, nc), kBlock, 0, c->stream>>>(uc, nullptr, nullptr, u, nullptr, s.nx, s.ny, s.nz);
-  else
-    k_restrict<double, 3><<<grid_for(c, nc), kBlock, 0, c->stream>>>(uc, nullptr, nullptr, u, nullptr, s.nx, s.ny, s.nz);
-  c->launches += 1;
+  {
+    Prof pr(c, FAS_K_RESTRICT, level, (double)s.cells());
+    if (c->p.dim == 2)
+      k_restrict<double, 2><<<grid_for(c, nc), kBlock, 0, c->stream>>>(uc, nullptr, nullptr, u, nullptr, s.nx, s.ny, s.nz);
+    else
+      k_restrict<double, 3><<<grid_for(c, nc), kBlock, 0, c->stream>>>(uc, nullptr, nullptr, u, nullptr, s.nx, s.ny, s.nz);
+  }
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   CUDA_TRY(cudaGetLastError());
   return FAS_OK;
@@ -736,13 +883,53 @@ fas_status fas_prolong_add(fas_ctx* c, int level, double* u, const double* cc) {
   STATUS_TRY(check_level(c, level, true));
   const LevelShape& s = c->shape[level];
   const int64_t nc = s.cells() >> c->p.dim;
-  if (c->p.dim == 2)
-    k_prolong<double, 2><<<grid_for(c, nc), kBlock, 0, c->stream>>>(u, cc, nullptr, s.nx, s.ny, s.nz);
-  else
-    k_prolong<double, 3><<<grid_for(c, nc), kBlock, 0, c->stream>>>(u, cc, nullptr, s.nx, s.ny, s.nz);
-  c->launches += 1;
+  {
+    Prof pr(c, FAS_K_PROLONG, level, (double)s.cells());
+    if (c->p.dim == 2)
+      k_prolong<double, 2><<<grid_for(c, nc), kBlock, 0, c->stream>>>(u, cc, nullptr, s.nx, s.ny, s.nz);
+    else
+      k_prolong<double, 3><<<grid_for(c, nc), kBlock, 0, c->stream>>>(u, cc, nullptr, s.nx, s.ny, s.nz);
+  }
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   CUDA_TRY(cudaGetLastError());
+  return FAS_OK;
+}
+
+fas_status fas_prof_enable(fas_ctx* c, int on) {
+  STATUS_TRY(check_ctx(c));
+  if (on) {
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->spans.clear();
+    c->pool_next = 0;
+  }
+  c->prof = on != 0;
+  return FAS_OK;
+}
+
+fas_status fas_prof_read(fas_ctx* c, fas_prof_record* out, int cap, int* count) {
+  STATUS_TRY(check_ctx(c));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  std::vector<fas_prof_record> agg;
+  for (const ProfSpan& sp : c->spans) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, sp.beg, sp.end));
+    fas_prof_record* rec = nullptr;
+    for (auto& a : agg)
+      if (a.family == sp.family && a.level == sp.level) rec = &a;
+    if (!rec) {
+      fas_prof_record z;
+      std::memset(&z, 0, sizeof(z));
+      z.family = sp.family;
+      z.level = sp.level;
+      agg.push_back(z);
+      rec = &agg.back();
+    }
+    rec->launches += 1;
+    rec->ms += ms;
+    rec->units += sp.units;
+  }
+  if (count) *count = (int)agg.size();
+  for (int k = 0; k < (int)agg.size() && k < cap && out; ++k) out[k] = agg[k];
   return FAS_OK;
 }
 

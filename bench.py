@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the FAS multigrid hot path on GB300.
+
+Workload (one "step"): 2D backward-Euler heat on an 8192^2 cell-centred grid of [0,1]^2, Neumann
+boundaries, kappa 1, dt 1e-4, 20 time steps from u0 = cos(pi x) cos(pi y) + 1e-2 U(-1,1) noise with a
+source of 16 Gaussians (sigma 0.02), every time step solved to 1e-10 relative residual by V(2,2)
+FAS cycles with X-MCGS smoothing (coarsest 4x4). Inputs are seeded synthetic fields (workloads/).
+
+Metric: Mcells*V-cycles/s = fine cells x fine-grid V-cycles done / seconds / 1e6 for the whole
+20-step run, mixed precision (float32 cycles inside float64 iterative refinement). The plain float64
+solve of the same run is measured beside it, with its time-to-solution ratio.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload (the solver has no
+cross-GPU step); value = cells x cycles summed over ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mcells*V-cycles/s to 1e-10 rel. residual (2D heat 8192^2, mixed precision)"
+UNIT = "Mcells*V-cycles/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192, help="cells per axis")
+    ap.add_argument("--heat-steps", type=int, default=20)
+    ap.add_argument("--inner", type=int, default=0, help="float32 cycles per refinement step (0: tune)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison arm")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        finally:
+            os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------------------------
+# algorithmic work per cell of each kernel family (bytes or float64 operations); see the design doc
+# ---------------------------------------------------------------------------------------------
+
+def kernel_work(family, level, inner_first_zero=True):
+    """(bound, per-cell work, unit) of a kernel family on a level of the mixed-precision solver.
+    float32 fused kernels: bytes that must cross HBM once (b = 4); float64 refinement kernels: FP64
+    FLOPs (DFMA counted as 2) for the residual, bytes for the update."""
+    b = 4.0
+    if family == "smooth":  # fused pre-smoothing: f (+u, +R(r)) in, u and R(u), R(r) out
+        if level == 0:
+            return "hbm", (2.5 if inner_first_zero else 3.5) * b, "B"
+        return "hbm", 4.5 * b, "B"
+    if family == "prolong":  # fused post-smoothing: u, f, u_c in; u out
+        return "hbm", 3.25 * b, "B"
+    if family == "ir":  # r = b - A u: 3 DADD + 2 DFMA per cell
+        return "alu", 7.0, "FLOP"
+    if family == "update":  # u += e: read u, e, write u
+        return "hbm", 20.0, "B"
+    return None, None, None
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2510_11152_gb300 as fas
+    from workloads import heat2d_large
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fas.load()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.n
+    w = heat2d_large(n=n, nsteps=args.heat_steps)
+    shape, h, dt, nsteps = w["shape"], w["h"], w["dt"], w["nsteps"]
+    cells = n * n
+    u0_d = torch.from_numpy(w["u0"]).to(dev)
+    f_d = torch.from_numpy(w["fsrc"]).to(dev)
+    u_d = torch.empty_like(u0_d)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(precision, inner=1):
+        return fas.fas_create(fas.make_params(shape, h, alpha=1.0, beta=dt, coarsest=4, precision=precision,
+                                              inner_cycles=inner), stream=stream)
+
+    def one_run(ctx, inner):
+        u_d.copy_(u0_d)
+        infos = fas.fas_heat_run(ctx, u_d, f_d, dt, nsteps)
+        return sum(i.cycles for i in infos) * inner, infos
+
+    # tune the float32 cycles per refinement step on one run each (time to solution decides)
+    inners = [args.inner] if args.inner > 0 else [1, 2, 3]
+    best = None
+    for inner in inners:
+        ctx = make(fas.FAS_MIXED, inner)
+        one_run(ctx, inner)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one_run(ctx, inner)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        if best is None or t < best[0]:
+            best = (t, inner, ctx)
+        else:
+            fas.fas_destroy(ctx)
+    _, inner, ctx = best
+
+    def timed(ctx, inner, steps, warmup):
+        for _ in range(warmup):
+            one_run(ctx, inner)
+        barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        fas.fas_launch_count(ctx, reset=True)
+        cycles, infos_all = 0, []
+        ev0.record(stream)
+        for _ in range(steps):
+            c, infos = one_run(ctx, inner)
+            cycles += c
+            infos_all.append(infos)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        return ms, cycles, fas.fas_launch_count(ctx), infos_all
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms, cycles, launches, infos_all = timed(ctx, inner, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms)
+    value = ws * cells * cycles / (ms_max / 1e3) / 1e6
+    last = infos_all[-1]
+    converged = all(i.converged for infos in infos_all for i in infos)
+    u_final = u_d.clone()
+
+    # float64 arm
+    fp64 = None
+    if not args.no_fp64:
+        ctx64 = make(fas.FAS_FP64)
+        ms64, cyc64, _, inf64 = timed(ctx64, 1, max(1, args.steps), max(1, min(args.warmup, 3)))
+        ms64 = max_over_ranks(ms64)
+        u64 = u_d.clone()
+        err = float((u_final - u64).abs().max().item() / u64.abs().max().item())
+        fp64 = {"value": ws * cells * cyc64 / (ms64 / 1e3) / 1e6, "unit": UNIT,
+                "ms_per_step": ms64 / max(1, args.steps),
+                "vcycles_per_run": cyc64 / max(1, args.steps),
+                "mixed_vs_fp64_rel_maxdiff": err,
+                "speedup_mixed_vs_fp64_time": (ms64 / max(1, args.steps)) / (ms / args.steps)}
+        fas.fas_destroy(ctx64)
+
+    # kernel timings: one instrumented run, CUDA events on the solver's stream
+    fas.fas_prof_enable(ctx, True)
+    one_run(ctx, inner)
+    recs = fas.fas_prof_read(ctx)
+    fas.fas_prof_enable(ctx, False)
+    total_ms = sum(r["ms"] for r in recs)
+    dom = max(recs, key=lambda r: r["ms"])
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    fp64_peak = 1.25  # TFLOP/s, nominal GB300 FP64 (FMA counted as 2)
+
+    def roofline_of(r):
+        bound, work, unit = kernel_work(r["family"], r["level"])
+        if bound is None:
+            return None
+        per_launch_units = r["units"] / r["launches"]
+        t = r["ms"] / r["launches"] / 1e3
+        if unit == "B":
+            ach = work * per_launch_units / t / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                    "traffic": None}
+        ach = work * per_launch_units / t / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                "traffic": None}
+
+    roof = roofline_of(dom) or {"bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s",
+                                "frac": None, "traffic": None}
+    roof.update({"kernel": "%s@level%d" % (dom["family"], dom["level"]),
+                 "share_of_kernel_time": dom["ms"] / total_ms if total_ms else None,
+                 "ms_per_launch": dom["ms"] / dom["launches"]})
+    kernels = sorted(({"kernel": "%s@L%d" % (r["family"], r["level"]), "launches": r["launches"],
+                       "ms": round(r["ms"], 4), "share": round(r["ms"] / total_ms, 4)} for r in recs),
+                     key=lambda d: -d["ms"])[:12]
+    # X-MCGS sweeps on the finest level: sweep-equivalent bytes 3b per cell per sweep (u in/out, f in)
+    xm = {}
+    for fam, name in (("smooth", "pre"), ("prolong", "post")):
+        r = [q for q in recs if q["family"] == fam and q["level"] == 0]
+        if r:
+            r = r[0]
+            t = r["ms"] / r["launches"] / 1e3
+            rf = roofline_of(r)
+            xm[name] = {"ms_per_launch": r["ms"] / r["launches"],
+                        "kernel_GBs": rf["achieved"], "kernel_frac": rf["frac"],
+                        "sweep_equiv_GBs": 2 * 3 * 4 * cells / t / 1e9}
+
+    # end to end through the host-buffer entry point (pinned host memory, copies inside the region)
+    e2e = None
+    try:
+        u0_h = torch.from_numpy(w["u0"]).pin_memory()
+        f_h = torch.from_numpy(w["fsrc"]).pin_memory()
+        out_h = torch.empty_like(u0_h).pin_memory()
+        a0, ah, fh = u0_h.numpy(), out_h.numpy(), f_h.numpy()
+        fas.fas_heat_run_host(ctx, a0, ah, fh, dt, nsteps)
+        barrier()
+        t0 = time.perf_counter()
+        cyc = 0
+        for _ in range(args.steps):
+            infos = fas.fas_heat_run_host(ctx, a0, ah, fh, dt, nsteps)
+            cyc += sum(i.cycles for i in infos) * inner
+        te = time.perf_counter() - t0
+        te = max_over_ranks(te)
+        e2e = {"value": ws * cells * cyc / te / 1e6, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * cells,
+               "d2h_bytes_per_step": 8 * cells, "ms_per_step": te * 1e3 / args.steps,
+               "matches_device_run": bool(np.array_equal(ah, u_final.cpu().numpy()))}
+    except Exception as exc:  # pragma: no cover - reported, not hidden
+        e2e = {"value": None, "unit": UNIT, "error": repr(exc)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "heat2d-8192x8192-neumann-dt1e-4-20steps-tol1e-10-V(2,2)-coarsest4",
+                       "grid": [n, n], "time_steps_per_run": nsteps, "precision": "mixed",
+                       "inner_float32_cycles": inner, "vcycles_per_run": cycles / args.steps,
+                       "l2": "inputs larger than L2 (512 MiB per float64 field)",
+                       "parallelism": "replicas" if ws > 1 else "single-gpu"},
+            "converged_all": converged, "last_step_info": last[-1].as_dict(),
+            "fp64": fp64, "roofline": roof, "xmcgs": xm, "kernels": kernels,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, n_cycles=1):
+    """The oracle as it stands, one float64 V(2,2) cycle on the first time step's system at full size
+    (bounded sample, about 20-40 s of single-threaded numpy)."""
+    from oracle import cell_centred as cc
+    op = cc.heat_operator(w["shape"], w["h"], w["dt"])
+    lev = cc.build_levels(op, 4)
+    b = w["u0"] + w["dt"] * w["fsrc"]
+    u = w["u0"].copy()
+    t0 = time.perf_counter()
+    for _ in range(n_cycles):
+        cc.vcycle(lev, u, b, cc.Params(coarsest=4))
+    t = time.perf_counter() - t0
+    cells = w["shape"][0] * w["shape"][1]
+    return {"value": cells * n_cycles / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d float64 V(2,2) cycle(s) of the numpy oracle on the first backward-Euler step of the "
+                      "%dx%d workload (%.1f s)" % (n_cycles, w["shape"][0], w["shape"][1], t)}
+
+
+def run_reference(args, ws, rank):
+    """The oracle timed on the host cores on the same metric; each step one oracle V-cycle on the
+    first time step's system, at a grid size chosen so the whole run stays within a few minutes."""
+    if rank != 0:
+        return
+    from oracle import cell_centred as cc
+    from workloads import heat2d_large
+    total = args.steps + args.warmup
+    n = args.n if total <= 6 else (args.n // 2 if total <= 24 else args.n // 4)
+    w = heat2d_large(n=n, nsteps=1)
+    op = cc.heat_operator(w["shape"], w["h"], w["dt"])
+    lev = cc.build_levels(op, 4)
+    b = w["u0"] + w["dt"] * w["fsrc"]
+    prm = cc.Params(coarsest=4)
+    u = w["u0"].copy()
+    for _ in range(args.warmup):
+        cc.vcycle(lev, u, b, prm)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cc.vcycle(lev, u, b, prm)
+    t = time.perf_counter() - t0
+    value = n * n * args.steps / t / 1e6
+    sample = "one float64 V(2,2) cycle of the numpy oracle per step on the first backward-Euler step of the " \
+             "heat workload at %dx%d (same recipe as the 8192^2 workload)" % (n, n)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "heat2d-8192x8192-neumann-dt1e-4-20steps-tol1e-10-V(2,2)-coarsest4",
+                       "sample_grid": [n, n]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -114,9 +114,11 @@ fas_status fas_solve(fas_ctx* ctx, double* u, const double* f, fas_info* info);
 fas_status fas_heat_run(fas_ctx* ctx, double* u, const double* fsrc, double dt, int nsteps,
                         fas_info* infos);
 
-/* fas_heat_run with HOST buffers: copies u (in/out) and fsrc to the device, runs, copies u back. */
-fas_status fas_heat_run_host(fas_ctx* ctx, double* u_host, const double* fsrc_host, double dt,
-                             int nsteps, fas_info* infos);
+/* fas_heat_run with HOST buffers (pinned memory gives the fastest copies): copies u0_host and
+ * fsrc_host (may be NULL) to device buffers the context keeps between calls, runs nsteps steps and
+ * copies the result to uT_host (may equal u0_host). Returns after the result is on the host. */
+fas_status fas_heat_run_host(fas_ctx* ctx, const double* u0_host, double* uT_host,
+                             const double* fsrc_host, double dt, int nsteps, fas_info* infos);
 
 /* --- single operators, for testing each kernel against the oracle ---------------------------- */
 
@@ -144,10 +146,11 @@ typedef enum {
   FAS_K_TAU = 3,         /* coarse source term f_c = R(r) + A_c R(u)                             */
   FAS_K_PROLONG = 4,     /* prolongation of the correction (+ post-smoothing when fused)         */
   FAS_K_COARSE = 5,      /* single-CTA V-cycle over the small levels                             */
-  FAS_K_IR = 6,          /* mixed precision: float64 update and residual                         */
+  FAS_K_IR = 6,          /* mixed precision: float64 residual r = b - A u, rounded to float32    */
   FAS_K_NORM = 7,        /* norms and means                                                     */
   FAS_K_OTHER = 8,       /* right-hand sides, fills, conversions                                */
-  FAS_K_NFAMILIES = 9
+  FAS_K_UPDATE = 9,      /* mixed precision: float64 u += e                                      */
+  FAS_K_NFAMILIES = 10
 } fas_kernel_family;
 
 /* Per (family, level) totals since the last fas_prof_enable(ctx, 1). */

@@ -82,7 +82,7 @@ def load(path: str | None = None):
         "fas_vcycle": (_I, [_P, _P, _P, ctypes.POINTER(fas_info)]),
         "fas_solve": (_I, [_P, _P, _P, ctypes.POINTER(fas_info)]),
         "fas_heat_run": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(fas_info)]),
-        "fas_heat_run_host": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(fas_info)]),
+        "fas_heat_run_host": (_I, [_P, _P, _P, _P, _D, _I, ctypes.POINTER(fas_info)]),
         "fas_residual": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(_D)]),
         "fas_smooth": (_I, [_P, _I, _P, _P, _I]),
         "fas_restrict": (_I, [_P, _I, _P, _P]),
@@ -207,16 +207,17 @@ def fas_heat_run(ctx: _Ctx, u, fsrc, dt: float, nsteps: int):
     return [infos[k] for k in range(nsteps)]
 
 
-def fas_heat_run_host(ctx: _Ctx, u_host, fsrc_host, dt: float, nsteps: int):
-    """Host numpy float64 arrays (u_host updated in place)."""
+def fas_heat_run_host(ctx: _Ctx, u0_host, uT_host, fsrc_host, dt: float, nsteps: int):
+    """Host float64 arrays (numpy, C-contiguous; pinned memory copies fastest). uT_host may be u0_host."""
     import numpy as np
     n = ctx.cells
-    for a, what in ((u_host, "u_host"), (fsrc_host, "fsrc_host")):
+    for a, what in ((u0_host, "u0_host"), (uT_host, "uT_host"), (fsrc_host, "fsrc_host")):
         if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n):
             raise TypeError("%s must be a C-contiguous float64 array of %d elements" % (what, n))
     infos = (fas_info * max(nsteps, 1))()
     fptr = None if fsrc_host is None else fsrc_host.ctypes.data
-    st = load().fas_heat_run_host(ctx.handle, u_host.ctypes.data, fptr, float(dt), int(nsteps), infos)
+    st = load().fas_heat_run_host(ctx.handle, u0_host.ctypes.data, uT_host.ctypes.data, fptr, float(dt),
+                                  int(nsteps), infos)
     _check(st, "fas_heat_run_host")
     return [infos[k] for k in range(nsteps)]
 
@@ -253,7 +254,7 @@ class fas_prof_record(ctypes.Structure):
                 ("ms", ctypes.c_double), ("units", ctypes.c_double)]
 
 
-FAMILIES = ["smooth", "residual", "restrict", "tau", "prolong", "coarse", "ir", "norm", "other"]
+FAMILIES = ["smooth", "residual", "restrict", "tau", "prolong", "coarse", "ir", "norm", "other", "update"]
 
 
 def fas_prof_enable(ctx: _Ctx, on: bool = True) -> None:

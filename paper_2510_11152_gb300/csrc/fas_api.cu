@@ -586,7 +586,7 @@ fas_status mixed_step(fas_ctx* c, double* u) {
     for (int k = 0; k < inner; ++k) vcycle<float>(c, H, H.u[0], H.f[0]);
   }
   {
-    Prof pr(c, FAS_K_IR, 0, (double)n);
+    Prof pr(c, FAS_K_UPDATE, 0, (double)n);
     k_ir_update<<<grid_for(c, n), kBlock, 0, c->stream>>>(u, H.u[0], n);
   }
   CUDA_TRY(cudaGetLastError());
@@ -774,6 +774,8 @@ fas_status fas_destroy(fas_ctx* c) {
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
   if (c->b) cudaFree(c->b);
   if (c->fproj) cudaFree(c->fproj);
+  if (c->host_u) cudaFree(c->host_u);
+  if (c->host_f) cudaFree(c->host_f);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   delete c;
   return FAS_OK;
@@ -815,25 +817,19 @@ fas_status fas_heat_run(fas_ctx* c, double* u, const double* fsrc, double dt, in
   return worst;
 }
 
-fas_status fas_heat_run_host(fas_ctx* c, double* u_host, const double* fsrc_host, double dt, int nsteps,
-                             fas_info* infos) {
+fas_status fas_heat_run_host(fas_ctx* c, const double* u0_host, double* uT_host, const double* fsrc_host, double dt,
+                             int nsteps, fas_info* infos) {
   STATUS_TRY(check_ctx(c));
-  if (!u_host) return fail(FAS_EINVAL, "fas_heat_run_host: null u");
+  if (!u0_host || !uT_host) return fail(FAS_EINVAL, "fas_heat_run_host: null u");
   const int64_t n = c->shape[0].cells();
-  double *du = nullptr, *df = nullptr;
-  CUDA_TRY(cudaMalloc(&du, n * sizeof(double)));
-  if (fsrc_host && cudaMalloc(&df, n * sizeof(double)) != cudaSuccess) {
-    cudaFree(du);
-    return fail(FAS_ENOMEM, "fas_heat_run_host: device buffers");
-  }
-  cudaMemcpyAsync(du, u_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-  if (df) cudaMemcpyAsync(df, fsrc_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-  fas_status st = fas_heat_run(c, du, df, dt, nsteps, infos);
-  cudaMemcpyAsync(u_host, du, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-  cudaError_t e = cudaStreamSynchronize(c->stream);
-  cudaFree(du);
-  if (df) cudaFree(df);
-  if (e != cudaSuccess) return fail(FAS_ECUDA, cudaGetErrorString(e));
+  if (!c->host_u) CUDA_TRY(cudaMalloc(&c->host_u, n * sizeof(double)));
+  if (fsrc_host && !c->host_f) CUDA_TRY(cudaMalloc(&c->host_f, n * sizeof(double)));
+  CUDA_TRY(cudaMemcpyAsync(c->host_u, u0_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (fsrc_host)
+    CUDA_TRY(cudaMemcpyAsync(c->host_f, fsrc_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  fas_status st = fas_heat_run(c, c->host_u, fsrc_host ? c->host_f : nullptr, dt, nsteps, infos);
+  CUDA_TRY(cudaMemcpyAsync(uT_host, c->host_u, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
   return st;
 }
 

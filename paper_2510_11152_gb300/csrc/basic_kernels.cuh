@@ -17,13 +17,12 @@ namespace fasmg {
 template <typename T, int DIM>
 __device__ __forceinline__ void smooth_colour_range(T* u, const T* f, const LevelDesc<T>& L, int colour,
                                                     int64_t t0, int64_t stride) {
-  const int hx = L.nx >> 1;
-  const int64_t half = (int64_t)hx * L.ny * L.nz;
+  const int lhx = L.lx - 1;
+  const int64_t half = ((int64_t)1 << (lhx + L.ly + L.lz));
   for (int64_t t = t0; t < half; t += stride) {
-    const int k = (int)(t % hx);
-    const int64_t rest = t / hx;
-    const int j = (int)(rest % L.ny);
-    const int l = (int)(rest / L.ny);
+    const int k = (int)(t & ((1 << lhx) - 1));
+    const int j = (int)((t >> lhx) & (L.ny - 1));
+    const int l = (int)(t >> (lhx + L.ly));
     const int i = 2 * k + ((colour + DIM + j + l) & 1);
     const int64_t idx = ((int64_t)l * L.ny + j) * L.nx + i;
     u[idx] = point_update<T, DIM>(u, f, L, idx, i, j, l);
@@ -37,10 +36,9 @@ __device__ __forceinline__ float residual_range(T* r, const T* u, const T* f, co
   const int64_t n = (int64_t)L.nx * L.ny * L.nz;
   float acc = 0.f;
   for (int64_t idx = t0; idx < n; idx += stride) {
-    const int i = (int)(idx % L.nx);
-    const int64_t rest = idx / L.nx;
-    const int j = (int)(rest % L.ny);
-    const int l = (int)(rest / L.ny);
+    const int i = (int)(idx & (L.nx - 1));
+    const int j = (int)((idx >> L.lx) & (L.ny - 1));
+    const int l = (int)(idx >> (L.lx + L.ly));
     const T rv = residual_point<T, DIM>(u, f, L, idx, i, j, l);
     if (r) r[idx] = rv;
     const float rs = (float)rv * nscale;
@@ -67,11 +65,11 @@ __device__ __forceinline__ void restrict_range(T* uc, T* uc0, T* fc, const T* u,
   const int nxc = nxf >> 1, nyc = nyf >> 1, nzc = DIM == 3 ? nzf >> 1 : 1;
   const int64_t nc = (int64_t)nxc * nyc * nzc;
   const int64_t sy = nxf, sz = (int64_t)nxf * nyf;
+  const int lxc = __ffs(nxc) - 1, lyc = __ffs(nyc) - 1;
   for (int64_t I = t0; I < nc; I += stride) {
-    const int ic = (int)(I % nxc);
-    const int64_t rest = I / nxc;
-    const int jc = (int)(rest % nyc);
-    const int lc = (int)(rest / nyc);
+    const int ic = (int)(I & (nxc - 1));
+    const int jc = (int)((I >> lxc) & (nyc - 1));
+    const int lc = (int)(I >> (lxc + lyc));
     const int64_t base = ((int64_t)(DIM == 3 ? 2 * lc : 0) * nyf + 2 * jc) * nxf + 2 * ic;
     if (u) {
       const T v = avg_children<T, DIM>(u, base, sy, sz);
@@ -88,10 +86,9 @@ __device__ __forceinline__ void tau_range(T* fc, const T* uc, const LevelDesc<T>
                                           int64_t stride) {
   const int64_t n = (int64_t)Lc.nx * Lc.ny * Lc.nz;
   for (int64_t idx = t0; idx < n; idx += stride) {
-    const int i = (int)(idx % Lc.nx);
-    const int64_t rest = idx / Lc.nx;
-    const int j = (int)(rest % Lc.ny);
-    const int l = (int)(rest / Lc.ny);
+    const int i = (int)(idx & (Lc.nx - 1));
+    const int j = (int)((idx >> Lc.lx) & (Lc.ny - 1));
+    const int l = (int)(idx >> (Lc.lx + Lc.ly));
     fc[idx] = fc[idx] + apply_point<T, DIM>(uc, Lc, idx, i, j, l);
   }
 }
@@ -103,11 +100,11 @@ __device__ __forceinline__ void prolong_range(T* u, const T* uc, const T* uc0, i
   const int nxc = nxf >> 1, nyc = nyf >> 1, nzc = DIM == 3 ? nzf >> 1 : 1;
   const int64_t nc = (int64_t)nxc * nyc * nzc;
   const int64_t sy = nxf, sz = (int64_t)nxf * nyf;
+  const int lxc = __ffs(nxc) - 1, lyc = __ffs(nyc) - 1;
   for (int64_t I = t0; I < nc; I += stride) {
-    const int ic = (int)(I % nxc);
-    const int64_t rest = I / nxc;
-    const int jc = (int)(rest % nyc);
-    const int lc = (int)(rest / nyc);
+    const int ic = (int)(I & (nxc - 1));
+    const int jc = (int)((I >> lxc) & (nyc - 1));
+    const int lc = (int)(I >> (lxc + lyc));
     const int64_t base = ((int64_t)(DIM == 3 ? 2 * lc : 0) * nyf + 2 * jc) * nxf + 2 * ic;
     const T c = uc0 ? uc[I] - uc0[I] : uc[I];
     u[base] += c;
@@ -190,9 +187,18 @@ __global__ void k_sub_mean(T* x, const T* y, int64_t n, const double* sum) {
   for (int64_t i = gtid(); i < n; i += gstride()) x[i] = y[i] - m;
 }
 
-// heat step right-hand side: b = u + dt * fsrc (fsrc may be null: b = u)
-__global__ void k_heat_rhs(double* b, const double* u, const double* fsrc, double dt, int64_t n) {
-  for (int64_t i = gtid(); i < n; i += gstride()) b[i] = fsrc ? fma(dt, fsrc[i], u[i]) : u[i];
+// heat step right-hand side: b = u + dt * fsrc (fsrc may be null: b = u), with the per-block partial
+// sums of b^2 (float squares) for ||b||
+__global__ void k_heat_rhs(double* b, const double* u, const double* fsrc, double dt, int64_t n, double* partials) {
+  float acc = 0.f;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    const double v = fsrc ? fma(dt, fsrc[i], u[i]) : u[i];
+    b[i] = v;
+    const float vf = (float)v;
+    acc = fmaf(vf, vf, acc);
+  }
+  const double s = block_sum((double)acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 // ---- mixed precision (iterative refinement): u += e, and r32 = (float)(b - A u) with its norm
@@ -206,10 +212,9 @@ __global__ void k_ir_residual(float* r32, const double* u, const double* b, Leve
   const int64_t n = (int64_t)L.nx * L.ny * L.nz;
   float acc = 0.f;
   for (int64_t idx = gtid(); idx < n; idx += gstride()) {
-    const int i = (int)(idx % L.nx);
-    const int64_t rest = idx / L.nx;
-    const int j = (int)(rest % L.ny);
-    const int l = (int)(rest / L.ny);
+    const int i = (int)(idx & (L.nx - 1));
+    const int j = (int)((idx >> L.lx) & (L.ny - 1));
+    const int l = (int)(idx >> (L.lx + L.ly));
     const float rv = (float)residual_point<double, DIM>(u, b, L, idx, i, j, l);
     r32[idx] = rv;
     const float rs = rv * nscale;
@@ -285,10 +290,10 @@ __global__ void k_kappa_weights(T* wx, T* wy, T* wz, T* rD, T* Dh, const double*
 }
 
 // ------------------------------------------------------------------------------------------------
-// Single-CTA V-cycle over levels l0..nlev-1 (the small levels, which cannot fill the GPU): the same
-// recursion as the host driver, with __syncthreads() between dependent steps. Level l0 works on
-// (utop, ftop); deeper levels on the context's buffers. The coarsest level is smoothed (paper) or,
-// when cinv is given, solved exactly by the dense inverse (pseudo-inverse when singular).
+// Arguments of the single-CTA V-cycle over levels l0..nlev-1 (the small levels, which cannot fill the
+// GPU): the same recursion as the host driver, with __syncthreads() between dependent steps. Level l0
+// is read from and written back to (utop, ftop). The coarsest level is smoothed (paper) or, when cinv
+// is given, solved exactly by the dense inverse (pseudo-inverse when singular).
 // ------------------------------------------------------------------------------------------------
 template <typename T>
 struct CoarseArgs {
@@ -311,51 +316,116 @@ __device__ void coarse_smooth(T* u, const T* f, const LevelDesc<T>& L, int sweep
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Single-CTA V-cycle with every level held in shared memory: levels l0..nlev-1 of u and f, and the
+// restricted start u0 of the coarser ones. Same steps and same per-point arithmetic as the grid-wide
+// kernels (the residual is evaluated per child inside the restriction instead of being stored
+// first), so the results are identical; the latency of each dependent step is a shared-memory round
+// trip instead of an L2 one.
+// ------------------------------------------------------------------------------------------------
+struct SmemLayout {
+  int64_t off_u[kMaxLevels], off_f[kMaxLevels], off_u0[kMaxLevels];  // element offsets
+  int64_t total;                                                      // elements
+};
+
 template <typename T, int DIM>
-__global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseArgs<T> A, T* utop, const T* ftop) {
+__device__ __forceinline__ void restrict_resid_range(T* uc, T* uc0, T* fc, const T* u, const T* f,
+                                                     const LevelDesc<T>& L, int64_t t0, int64_t stride) {
+  const int nxf = L.nx, nyf = L.ny, nzf = L.nz;
+  const int nxc = nxf >> 1, nyc = nyf >> 1, nzc = DIM == 3 ? nzf >> 1 : 1;
+  const int64_t nc = (int64_t)nxc * nyc * nzc;
+  const int64_t sy = nxf, sz = (int64_t)nxf * nyf;
+  const int lxc = L.lx - 1, lyc = L.ly - 1;
+  for (int64_t I = t0; I < nc; I += stride) {
+    const int ic = (int)(I & (nxc - 1));
+    const int jc = (int)((I >> lxc) & (nyc - 1));
+    const int lc = (int)(I >> (lxc + lyc));
+    const int i0 = 2 * ic, j0 = 2 * jc, l0 = DIM == 3 ? 2 * lc : 0;
+    const int64_t base = ((int64_t)l0 * nyf + j0) * nxf + i0;
+    const T v = avg_children<T, DIM>(u, base, sy, sz);
+    uc[I] = v;
+    uc0[I] = v;
+    T r[8];
+#pragma unroll
+    for (int k = 0; k < (DIM == 3 ? 8 : 4); ++k) {
+      const int di = k & 1, dj = (k >> 1) & 1, dl = (k >> 2) & 1;
+      const int64_t idx = base + di + dj * sy + dl * sz;
+      r[k] = residual_point<T, DIM>(u, f, L, idx, i0 + di, j0 + dj, l0 + dl);
+    }
+    // same association as avg_children: (c00 + c01) + (c10 + c11) [+ the upper z layer]
+    T sr = (r[0] + r[1]) + (r[2] + r[3]);
+    if (DIM == 3) {
+      const T s2 = (r[4] + r[5]) + (r[6] + r[7]);
+      fc[I] = (sr + s2) * T(0.125);
+    } else {
+      fc[I] = sr * T(0.25);
+    }
+  }
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayout S, T* utop, const T* ftop) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
   const int last = A.nlev - 1;
-  // descend
+  // level descriptors of levels l0..last, copied after the field arrays (every stencil reads them)
+  LevelDesc<T>* sdesc = reinterpret_cast<LevelDesc<T>*>(smem_raw + S.total * sizeof(T)) - A.l0;
+  {
+    const int words = (int)((A.nlev - A.l0) * sizeof(LevelDesc<T>) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(A.desc + A.l0);
+    int* dst = reinterpret_cast<int*>(sdesc + A.l0);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+  }
+  __syncthreads();
+  {
+    const LevelDesc<T>& L = sdesc[A.l0];
+    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      sm[S.off_u[A.l0] + i] = utop[i];
+      sm[S.off_f[A.l0] + i] = ftop[i];
+    }
+  }
+  __syncthreads();
   for (int l = A.l0; l < last; ++l) {
-    const LevelDesc<T>& L = A.desc[l];
-    const LevelDesc<T>& Lc = A.desc[l + 1];
-    T* u = l == A.l0 ? utop : A.u[l];
-    const T* f = l == A.l0 ? ftop : A.f[l];
+    const LevelDesc<T>& L = sdesc[l];
+    T* u = sm + S.off_u[l];
+    const T* f = sm + S.off_f[l];
     coarse_smooth<T, DIM>(u, f, L, A.nu1);
-    residual_range<T, DIM>(A.r[l], u, f, L, 1.f, threadIdx.x, blockDim.x);
+    restrict_resid_range<T, DIM>(sm + S.off_u[l + 1], sm + S.off_u0[l + 1], sm + S.off_f[l + 1], u, f, L,
+                                 threadIdx.x, blockDim.x);
     __syncthreads();
-    restrict_range<T, DIM>(A.u[l + 1], A.u0[l + 1], A.f[l + 1], u, A.r[l], L.nx, L.ny, L.nz, threadIdx.x,
-                           blockDim.x);
-    __syncthreads();
-    tau_range<T, DIM>(A.f[l + 1], A.u[l + 1], Lc, threadIdx.x, blockDim.x);
+    tau_range<T, DIM>(sm + S.off_f[l + 1], sm + S.off_u[l + 1], sdesc[l + 1], threadIdx.x, blockDim.x);
     __syncthreads();
   }
-  // coarsest level
   {
-    const LevelDesc<T>& L = A.desc[last];
-    T* u = last == A.l0 ? utop : A.u[last];
-    const T* f = last == A.l0 ? ftop : A.f[last];
-    if (A.cinv) {
+    const LevelDesc<T>& L = sdesc[last];
+    T* u = sm + S.off_u[last];
+    const T* f = sm + S.off_f[last];
+    if (A.cinv) {  // coarsest level of at most 1024 cells (checked on the host): one cell per thread
       const int n = L.nx * L.ny * L.nz;
-      for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      const int p = threadIdx.x;
+      if (p < n) {
         T acc = T(0);
         for (int q = 0; q < n; ++q) acc = fma(A.cinv[(int64_t)p * n + q], f[q], acc);
-        A.r[last][p] = acc;
+        u[p] = acc;
       }
-      __syncthreads();
-      for (int p = threadIdx.x; p < n; p += blockDim.x) u[p] = A.r[last][p];
       __syncthreads();
     } else {
       coarse_smooth<T, DIM>(u, f, L, A.nuc);
     }
   }
-  // ascend
   for (int l = last - 1; l >= A.l0; --l) {
-    const LevelDesc<T>& L = A.desc[l];
-    T* u = l == A.l0 ? utop : A.u[l];
-    const T* f = l == A.l0 ? ftop : A.f[l];
-    prolong_range<T, DIM>(u, A.u[l + 1], A.u0[l + 1], L.nx, L.ny, L.nz, threadIdx.x, blockDim.x);
+    const LevelDesc<T>& L = sdesc[l];
+    T* u = sm + S.off_u[l];
+    const T* f = sm + S.off_f[l];
+    prolong_range<T, DIM>(u, sm + S.off_u[l + 1], sm + S.off_u0[l + 1], L.nx, L.ny, L.nz, threadIdx.x, blockDim.x);
     __syncthreads();
     coarse_smooth<T, DIM>(u, f, L, A.nu2);
+  }
+  {
+    const LevelDesc<T>& L = sdesc[A.l0];
+    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) utop[i] = sm[S.off_u[A.l0] + i];
   }
 }
 

@@ -25,7 +25,8 @@ constexpr int kClasses = 64;  // 2^(2*dim) boundary classes, dim <= 3
 
 template <typename T>
 struct LevelDesc {
-  int nx, ny, nz;  // cells per axis (nz = 1 in 2D)
+  int nx, ny, nz;  // cells per axis (nz = 1 in 2D), powers of two
+  int lx, ly, lz;  // their base-2 logarithms (index decomposition by shifts)
   int varkappa;    // 1: use the per-cell arrays below
   T h2, ih2;       // h^2, 1/h^2
   T c;             // beta kappa / h^2 (constant kappa)

@@ -23,6 +23,8 @@ struct Hier {
   std::vector<T*> u, f, r, u0;
   std::vector<T*> u2, rc;  // fused path: second u buffer (ping-pong) and R(r) from the finer level
   int nfast = 0;           // levels 0..nfast-1 use the fused kernels
+  SmemLayout smem;         // shared-memory layout of the single-CTA kernel (levels >= switch_level)
+  size_t smem_bytes = 0;
   T** d_u = nullptr;
   T** d_f = nullptr;
   T** d_r = nullptr;

@@ -47,6 +47,8 @@ constexpr int kBlock = 256;
 constexpr int kCoarseThreads = 1024;
 constexpr int64_t kSwitchCells2D = 16384;  // levels at or below this size run in one CTA
 constexpr int64_t kSwitchCells3D = 4096;
+constexpr size_t kCoarseSmemMax = 200 * 1024;    // field arrays of the single-CTA kernel
+constexpr size_t kCoarseSmemLimit = 227 * 1024;  // with its level descriptors (per-CTA maximum)
 
 int grid_for(const fas_ctx* c, int64_t work) {
   int64_t g = (work + kBlock - 1) / kBlock;
@@ -102,6 +104,14 @@ LevelDesc<T> make_desc(const fas_params& p, const LevelShape& s) {
   L.nx = s.nx;
   L.ny = s.ny;
   L.nz = s.nz;
+  auto lg = [](int v) {
+    int k = 0;
+    while ((1 << k) < v) ++k;
+    return k;
+  };
+  L.lx = lg(s.nx);
+  L.ly = lg(s.ny);
+  L.lz = lg(s.nz);
   L.varkappa = p.kappa != nullptr;
   const double h2 = s.h * s.h;
   L.h2 = (T)h2;
@@ -221,13 +231,38 @@ fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers)
   H.nlev = c->nlev;
   H.desc.clear();
   for (int l = 0; l < c->nlev; ++l) H.desc.push_back(make_desc<T>(p, c->shape[l]));
+  // single-CTA switch level: the first level small enough that the GPU cannot be filled and whose
+  // whole sub-hierarchy (u, f on every level, u0 below it) fits in the CTA's shared memory
   const int64_t sw_cells = p.dim == 2 ? kSwitchCells2D : kSwitchCells3D;
   H.switch_level = c->nlev - 1;
-  for (int l = 0; l < c->nlev; ++l)
-    if (c->shape[l].cells() <= sw_cells) {
+  for (int l = 0; l < c->nlev; ++l) {
+    if (c->shape[l].cells() > sw_cells) continue;
+    int64_t elems = 2 * c->shape[l].cells();
+    for (int k = l + 1; k < c->nlev; ++k) elems += 3 * c->shape[k].cells();
+    if ((size_t)elems * sizeof(T) <= kCoarseSmemMax) {
       H.switch_level = l;
       break;
     }
+  }
+  {
+    int64_t off = 0;
+    for (int l = H.switch_level; l < c->nlev; ++l) {
+      const int64_t n = c->shape[l].cells();
+      const int64_t pad = (16 / sizeof(T));  // keep every array 16-byte aligned
+      H.smem.off_u[l] = off;
+      off += (n + pad - 1) / pad * pad;
+      H.smem.off_f[l] = off;
+      off += (n + pad - 1) / pad * pad;
+      if (l > H.switch_level) {
+        H.smem.off_u0[l] = off;
+        off += (n + pad - 1) / pad * pad;
+      }
+    }
+    H.smem.total = off;
+    H.smem_bytes = (size_t)off * sizeof(T) + (size_t)(c->nlev - H.switch_level) * sizeof(LevelDesc<T>);
+    if (H.smem_bytes > kCoarseSmemLimit)
+      return fail(FAS_EUNSUPPORTED, "coarsest levels do not fit in shared memory");
+  }
   // per-cell diffusivity: kappa on every level (cell averages), then weights per level
   std::vector<double> cwx, cwy, cwz, cDh;  // coarsest level, for the dense inverse
   if (p.kappa) {
@@ -388,8 +423,9 @@ void launch_residual(fas_ctx* c, const LevelDesc<T>& L, int level, T* r, const T
 }
 
 template <typename T, int DIM>
-void launch_coarse(fas_ctx* c, Hier<T>& H, int l0, T* utop, const T* ftop) {
+fas_status launch_coarse(fas_ctx* c, Hier<T>& H, int l0, T* utop, const T* ftop) {
   const fas_params& p = c->p;
+  if (l0 != H.switch_level) return fail(FAS_ECUDA, "single-CTA kernel launched above its shared-memory level");
   CoarseArgs<T> A;
   A.desc = H.d_desc;
   A.u = H.d_u;
@@ -402,19 +438,26 @@ void launch_coarse(fas_ctx* c, Hier<T>& H, int l0, T* utop, const T* ftop) {
   A.nu1 = p.nu1;
   A.nu2 = p.nu2;
   A.nuc = p.nu_coarse > 0 ? p.nu_coarse : p.nu1;
+  static bool attr_set = false;  // per template instantiation
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_coarse_smem<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemLimit);
+    attr_set = true;
+  }
   Prof pr(c, FAS_K_COARSE, l0, (double)c->shape[l0].cells());
-  k_coarse_vcycle<T, DIM><<<1, kCoarseThreads, 0, c->stream>>>(A, utop, ftop);
+  k_coarse_smem<T, DIM><<<1, kCoarseThreads, H.smem_bytes, c->stream>>>(A, H.smem, utop, ftop);
+  return FAS_OK;
 }
 
-// One V-cycle through the per-operation kernels (any value type, 2D or 3D).
+// Levels lfrom..switch-1 through the per-operation kernels around the single-CTA kernel (any value
+// type, 2D or 3D). Level lfrom works on (utop, ftop); deeper levels on the hierarchy's buffers.
 template <typename T, int DIM>
-void vcycle_basic(fas_ctx* c, Hier<T>& H, T* utop, const T* ftop) {
+fas_status vcycle_basic_from(fas_ctx* c, Hier<T>& H, int lfrom, T* utop, const T* ftop) {
   const fas_params& p = c->p;
   const int sw = H.switch_level;
-  for (int l = 0; l < sw; ++l) {
+  for (int l = lfrom; l < sw; ++l) {
     const LevelDesc<T>& L = H.desc[l];
-    T* u = l == 0 ? utop : H.u[l];
-    const T* f = l == 0 ? ftop : H.f[l];
+    T* u = l == lfrom ? utop : H.u[l];
+    const T* f = l == lfrom ? ftop : H.f[l];
     launch_smooth<T, DIM>(c, L, l, u, f, p.nu1);
     const int64_t n = (int64_t)L.nx * L.ny * L.nz;
     {
@@ -432,11 +475,11 @@ void vcycle_basic(fas_ctx* c, Hier<T>& H, T* utop, const T* ftop) {
       k_tau<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.f[l + 1], H.u[l + 1], H.desc[l + 1]);
     }
   }
-  launch_coarse<T, DIM>(c, H, sw, sw == 0 ? utop : H.u[sw], sw == 0 ? ftop : H.f[sw]);
-  for (int l = sw - 1; l >= 0; --l) {
+  STATUS_TRY((launch_coarse<T, DIM>(c, H, sw, sw == lfrom ? utop : H.u[sw], sw == lfrom ? ftop : H.f[sw])));
+  for (int l = sw - 1; l >= lfrom; --l) {
     const LevelDesc<T>& L = H.desc[l];
-    T* u = l == 0 ? utop : H.u[l];
-    const T* f = l == 0 ? ftop : H.f[l];
+    T* u = l == lfrom ? utop : H.u[l];
+    const T* f = l == lfrom ? ftop : H.f[l];
     const int64_t n = (int64_t)L.nx * L.ny * L.nz;
     {
       Prof pr(c, FAS_K_PROLONG, l, (double)n);
@@ -445,23 +488,30 @@ void vcycle_basic(fas_ctx* c, Hier<T>& H, T* utop, const T* ftop) {
     }
     launch_smooth<T, DIM>(c, L, l, u, f, p.nu2);
   }
+  return FAS_OK;
 }
 
-// rows per warp segment of the fused kernels: a multiple of 8 (row pairs stay aligned)
-int seg_rows(const fas_ctx* c) {
-  const int s = c->p.seg_rows > 0 ? c->p.seg_rows : 128;
-  return std::max(8, (s + 7) / 8 * 8);
+// Rows per warp segment of the fused kernels on a level: a multiple of 8 (row pairs stay aligned),
+// chosen so that the level's strips x segments fill about one wave of 16 warps per SM (shorter
+// segments recompute more halo rows, longer ones leave SMs idle), at most 128; seg_rows overrides.
+int seg_for_level(const fas_ctx* c, int nx, int ny) {
+  if (c->p.seg_rows > 0) return std::max(8, (c->p.seg_rows + 7) / 8 * 8);
+  const int64_t nstrips = (nx + kStripOut - 1) / kStripOut;
+  const int64_t target = (int64_t)c->sm_count * 16;
+  const int64_t seg = ((int64_t)ny * nstrips + target - 1) / target;  // rounded up: at most one wave
+  return (int)std::max<int64_t>(8, std::min<int64_t>(128, (seg + 7) / 8 * 8));
 }
 
 // One float32 V-cycle through the sweep-fused 2D kernels on levels 0..nfast-1 (ping-pong buffers u/u2,
 // R(r) in rc), the per-operation tau kernel and the single-CTA kernel below. Result in H.u[0].
 // zero_init: the level-0 initial guess is 0 (H.u[0] is not read).
-fas_status vcycle_fast(fas_ctx* c, Hier<float>& H, bool zero_init) {
+// u64 (nullable): add the result to this float64 field instead of storing it in H.u[0].
+fas_status vcycle_fast(fas_ctx* c, Hier<float>& H, bool zero_init, double* u64) {
   const fas_params& p = c->p;
   const int nf = H.nfast;
-  const int seg = seg_rows(c);
   for (int l = 0; l < nf; ++l) {
     const LevelDesc<float>& L = H.desc[l];
+    const int seg = seg_for_level(c, L.nx, L.ny);
     const bool tau = l > 0;
     float* rc_next = (l + 1 == nf) ? H.f[l + 1] : H.rc[l + 1];
     Prof pr(c, FAS_K_SMOOTH, l, (double)c->shape[l].cells());
@@ -474,22 +524,23 @@ fas_status vcycle_fast(fas_ctx* c, Hier<float>& H, bool zero_init) {
     Prof pr(c, FAS_K_TAU, nf, (double)nc);
     k_tau<float, 2><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.f[nf], H.u[nf], H.desc[nf]);
   }
-  launch_coarse<float, 2>(c, H, nf, H.u[nf], H.f[nf]);
+  // levels between the fused ones and the single-CTA level (narrow grids), then the small levels
+  STATUS_TRY((vcycle_basic_from<float, 2>(c, H, nf, H.u[nf], H.f[nf])));
   for (int l = nf - 1; l >= 0; --l) {
     const LevelDesc<float>& L = H.desc[l];
+    const int seg = seg_for_level(c, L.nx, L.ny);
     Prof pr(c, FAS_K_PROLONG, l, (double)c->shape[l].cells());
-    cudaError_t e = launch_stream2d_post(H.u2[l], H.f[l], H.u[l + 1], H.u[l], L, p.nu2, seg, c->stream);
+    cudaError_t e = launch_stream2d_post(H.u2[l], H.f[l], H.u[l + 1], H.u[l], l == 0 ? u64 : nullptr, L, p.nu2, seg,
+                                         c->stream);
     if (e != cudaSuccess) return fail(FAS_ECUDA, std::string("stream2d post: ") + cudaGetErrorString(e));
   }
   return FAS_OK;
 }
 
 template <typename T>
-void vcycle(fas_ctx* c, Hier<T>& H, T* u, const T* f) {
-  if (c->p.dim == 2)
-    vcycle_basic<T, 2>(c, H, u, f);
-  else
-    vcycle_basic<T, 3>(c, H, u, f);
+fas_status vcycle(fas_ctx* c, Hier<T>& H, T* u, const T* f) {
+  if (c->p.dim == 2) return vcycle_basic_from<T, 2>(c, H, 0, u, f);
+  return vcycle_basic_from<T, 3>(c, H, 0, u, f);
 }
 
 fas_status sync_read(fas_ctx* c, double* out) {
@@ -580,12 +631,11 @@ fas_status mixed_step(fas_ctx* c, double* u) {
   const int inner = c->p.inner_cycles > 0 ? c->p.inner_cycles : 1;
   Hier<float>& H = c->h32;
   if (H.nfast > 0) {
-    for (int k = 0; k < inner; ++k) STATUS_TRY(vcycle_fast(c, H, k == 0));
+    // the last cycle's post-smoothing kernel adds its result to u in float64
+    for (int k = 0; k < inner; ++k) STATUS_TRY(vcycle_fast(c, H, k == 0, k == inner - 1 ? u : nullptr));
   } else {
     CUDA_TRY(cudaMemsetAsync(H.u[0], 0, n * sizeof(float), c->stream));
-    for (int k = 0; k < inner; ++k) vcycle<float>(c, H, H.u[0], H.f[0]);
-  }
-  {
+    for (int k = 0; k < inner; ++k) STATUS_TRY(vcycle<float>(c, H, H.u[0], H.f[0]));
     Prof pr(c, FAS_K_UPDATE, 0, (double)n);
     k_ir_update<<<grid_for(c, n), kBlock, 0, c->stream>>>(u, H.u[0], n);
   }
@@ -593,18 +643,28 @@ fas_status mixed_step(fas_ctx* c, double* u) {
   return FAS_OK;
 }
 
-fas_status solve_impl(fas_ctx* c, double* u, const double* f_in, fas_info* info, int max_cycles) {
+// fn_known (nullable): ||f||_2 already computed by the caller (singular problems recompute it)
+fas_status solve_impl(fas_ctx* c, double* u, const double* f_in, fas_info* info, int max_cycles,
+                      const double* fn_known = nullptr) {
   const fas_params& p = c->p;
   const int64_t n = c->shape[0].cells();
   const double* f = f_in;
   if (c->singular) {
     STATUS_TRY(remove_mean(c, c->fproj, f_in));
     f = c->fproj;
+    fn_known = nullptr;
   }
   double fn = 0.0;
-  STATUS_TRY(norm_of(c, f, 1.f, &fn));
+  if (fn_known) {
+    fn = *fn_known;
+  } else {
+    STATUS_TRY(norm_of(c, f, 1.f, &fn));
+  }
+  // float squares are exact enough for a stopping test while the rms stays far from the float range
+  // limits; otherwise the norm is recomputed with a power-of-two scale
+  const double rms = fn / std::sqrt((double)n);
+  if (!(rms > 1e-15 && rms < 1e15)) STATUS_TRY(norm_of(c, f, pick_scale(fn, n), &fn));
   const float ns = pick_scale(fn, n);
-  if (ns != 1.f) STATUS_TRY(norm_of(c, f, ns, &fn));
   const bool mixed = p.precision == FAS_MIXED;
   double rn = 0.0;
   if (mixed) {
@@ -623,7 +683,7 @@ fas_status solve_impl(fas_ctx* c, double* u, const double* f_in, fas_info* info,
     if (mixed) {
       STATUS_TRY(mixed_step(c, u));
     } else {
-      vcycle<double>(c, c->h64, u, f);
+      STATUS_TRY(vcycle<double>(c, c->h64, u, f));
     }
     if (c->singular) STATUS_TRY(remove_mean(c, u, u));
     if (mixed) {
@@ -804,12 +864,19 @@ fas_status fas_heat_run(fas_ctx* c, double* u, const double* fsrc, double dt, in
   if (!c->b) CUDA_TRY(cudaMalloc(&c->b, n * sizeof(double)));
   fas_status worst = FAS_OK;
   for (int s = 0; s < nsteps; ++s) {
+    const int g = grid_for(c, n);
     {
       Prof pr(c, FAS_K_OTHER, 0, (double)n);
-      k_heat_rhs<<<grid_for(c, n), kBlock, 0, c->stream>>>(c->b, u, fsrc, dt, n);
+      k_heat_rhs<<<g, kBlock, 0, c->stream>>>(c->b, u, fsrc, dt, n, c->partials);
     }
+    {
+      Prof pr(c, FAS_K_NORM, 0, 0.0);
+      k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0);
+    }
+    double bn = 0.0;
+    STATUS_TRY(sync_read(c, &bn));
     fas_info inf;
-    fas_status st = solve_impl(c, u, c->b, &inf, c->p.kmax);
+    fas_status st = solve_impl(c, u, c->b, &inf, c->p.kmax, &bn);
     if (infos) infos[s] = inf;
     if (st != FAS_OK && st != FAS_ENOTCONV) return st;
     if (st == FAS_ENOTCONV) worst = st;

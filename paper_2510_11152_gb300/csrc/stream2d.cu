@@ -35,10 +35,6 @@ constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kWin = 8;  // register window rows (power of two, even)
 
-__device__ __forceinline__ int cls2(int x, int y, int nx, int ny) {
-  return (x == 0) | ((x == nx - 1) << 1) | ((y == 0) << 2) | ((y == ny - 1) << 3);
-}
-
 struct StripGeo {
   int x0;   // first column of the strip (may be negative)
   int xl;   // first column of this lane's 4 cells
@@ -70,63 +66,97 @@ __device__ __forceinline__ void st4(float* base, int64_t off, float4 v) {
   *reinterpret_cast<float4*>(base + off) = v;
 }
 
-// Gauss-Seidel update of one cell (same expression as point_update in common.cuh).
-__device__ __forceinline__ float gs(float w, float e, float s, float n, float fv, int x, int y,
-                                   const LevelDesc<float>& L, float old) {
+// Per-lane stencil constants: the x-boundary flags of the lane's 4 cells and, for rows away from the
+// y boundary, their class constants in registers (no indexed constant loads on the common path).
+struct LaneCoef {
+  int xf;  // x-boundary flags of the 4 cells, 2 bits each
+  float a[4], b[4];
+};
+
+__device__ __forceinline__ LaneCoef lane_coef(int xl, const LevelDesc<float>& L) {
+  LaneCoef q;
+  q.xf = 0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int x = xl + v;
+    const int fl = (x == 0) | ((x == L.nx - 1) << 1);
+    q.xf |= fl << (2 * v);
+    q.a[v] = L.a[fl];
+    q.b[v] = L.b[fl];
+  }
+  return q;
+}
+
+template <int V>
+__device__ __forceinline__ int xflag(const LaneCoef& q) {
+  return (q.xf >> (2 * V)) & 3;
+}
+
+__device__ __forceinline__ int yflags(int y, int ny) { return ((y == 0) << 2) | ((y == ny - 1) << 3); }
+
+// Gauss-Seidel update of cell v of the lane (same expression as point_update in common.cuh).
+template <bool FAST, int V>
+__device__ __forceinline__ float gs(float w, float e, float s, float n, float fv, int yf, const LaneCoef& q,
+                                    const LevelDesc<float>& L, bool in, float old) {
   const float nb = (w + e) + (s + n);
-  const int c = cls2(x, y, L.nx, L.ny);
-  const float v = fmaf(L.a[c], nb, L.b[c] * fv);
-  return (x >= 0 && x < L.nx) ? v : old;
+  float a = q.a[V], b = q.b[V];
+  if (FAST) return fmaf(a, nb, b * fv);
+  if (yf) {
+    a = L.a[xflag<V>(q) | yf];
+    b = L.b[xflag<V>(q) | yf];
+  }
+  const float val = fmaf(a, nb, b * fv);
+  return in ? val : old;
+}
+
+template <bool FAST, int V>
+__device__ __forceinline__ float dcoef(int yf, const LaneCoef& q, const LevelDesc<float>& L) {
+  return FAST ? L.d[0] : L.d[xflag<V>(q) | yf];
 }
 
 // One colour phase on a row: PAR = 0 updates cells v = 0, 2 of the lane; PAR = 1 cells v = 1, 3.
-template <int PAR>
-__device__ __forceinline__ void phase_row(float4& c, const float4& s, const float4& n, const float4& fv, int xl,
-                                          int y, const LevelDesc<float>& L) {
+template <bool FAST, int PAR>
+__device__ __forceinline__ void phase_row(float4& c, const float4& s, const float4& n, const float4& fv, int y,
+                                          const LaneCoef& q, const LevelDesc<float>& L, bool in) {
+  const int yf = FAST ? 0 : yflags(y, L.ny);
   if (PAR == 0) {
     const float wv = __shfl_up_sync(kFull, c.w, 1);
-    c.x = gs(wv, c.y, s.x, n.x, fv.x, xl, y, L, c.x);
-    c.z = gs(c.y, c.w, s.z, n.z, fv.z, xl + 2, y, L, c.z);
+    c.x = gs<FAST, 0>(wv, c.y, s.x, n.x, fv.x, yf, q, L, in, c.x);
+    c.z = gs<FAST, 2>(c.y, c.w, s.z, n.z, fv.z, yf, q, L, in, c.z);
   } else {
     const float ev = __shfl_down_sync(kFull, c.x, 1);
-    c.y = gs(c.x, c.z, s.y, n.y, fv.y, xl + 1, y, L, c.y);
-    c.w = gs(c.z, ev, s.w, n.w, fv.w, xl + 3, y, L, c.w);
+    c.y = gs<FAST, 1>(c.x, c.z, s.y, n.y, fv.y, yf, q, L, in, c.y);
+    c.w = gs<FAST, 3>(c.z, ev, s.w, n.w, fv.w, yf, q, L, in, c.w);
   }
 }
 
 // (A u) on the 4 cells of a row (same expression as apply_point).
-__device__ __forceinline__ float4 apply_row(const float4& c, const float4& s, const float4& n, int xl, int y,
-                                            const LevelDesc<float>& L) {
+template <bool FAST>
+__device__ __forceinline__ float4 apply_row(const float4& c, const float4& s, const float4& n, int y,
+                                            const LaneCoef& q, const LevelDesc<float>& L) {
+  const int yf = FAST ? 0 : yflags(y, L.ny);
   const float wv = __shfl_up_sync(kFull, c.w, 1);
   const float ev = __shfl_down_sync(kFull, c.x, 1);
   float4 o;
-  int k;
-  k = cls2(xl, y, L.nx, L.ny);
-  o.x = fmaf(L.d[k], c.x, -L.c * ((wv + c.y) + (s.x + n.x)));
-  k = cls2(xl + 1, y, L.nx, L.ny);
-  o.y = fmaf(L.d[k], c.y, -L.c * ((c.x + c.z) + (s.y + n.y)));
-  k = cls2(xl + 2, y, L.nx, L.ny);
-  o.z = fmaf(L.d[k], c.z, -L.c * ((c.y + c.w) + (s.z + n.z)));
-  k = cls2(xl + 3, y, L.nx, L.ny);
-  o.w = fmaf(L.d[k], c.w, -L.c * ((c.z + ev) + (s.w + n.w)));
+  o.x = fmaf(dcoef<FAST, 0>(yf, q, L), c.x, -L.c * ((wv + c.y) + (s.x + n.x)));
+  o.y = fmaf(dcoef<FAST, 1>(yf, q, L), c.y, -L.c * ((c.x + c.z) + (s.y + n.y)));
+  o.z = fmaf(dcoef<FAST, 2>(yf, q, L), c.z, -L.c * ((c.y + c.w) + (s.z + n.z)));
+  o.w = fmaf(dcoef<FAST, 3>(yf, q, L), c.w, -L.c * ((c.z + ev) + (s.w + n.w)));
   return o;
 }
 
 // r = f - A u on the 4 cells of a row (same expression as residual_point).
+template <bool FAST>
 __device__ __forceinline__ float4 resid_row(const float4& c, const float4& s, const float4& n, const float4& fv,
-                                            int xl, int y, const LevelDesc<float>& L) {
+                                            int y, const LaneCoef& q, const LevelDesc<float>& L) {
+  const int yf = FAST ? 0 : yflags(y, L.ny);
   const float wv = __shfl_up_sync(kFull, c.w, 1);
   const float ev = __shfl_down_sync(kFull, c.x, 1);
   float4 o;
-  int k;
-  k = cls2(xl, y, L.nx, L.ny);
-  o.x = fmaf(L.c, (wv + c.y) + (s.x + n.x), fmaf(-L.d[k], c.x, fv.x));
-  k = cls2(xl + 1, y, L.nx, L.ny);
-  o.y = fmaf(L.c, (c.x + c.z) + (s.y + n.y), fmaf(-L.d[k], c.y, fv.y));
-  k = cls2(xl + 2, y, L.nx, L.ny);
-  o.z = fmaf(L.c, (c.y + c.w) + (s.z + n.z), fmaf(-L.d[k], c.z, fv.z));
-  k = cls2(xl + 3, y, L.nx, L.ny);
-  o.w = fmaf(L.c, (c.z + ev) + (s.w + n.w), fmaf(-L.d[k], c.w, fv.w));
+  o.x = fmaf(L.c, (wv + c.y) + (s.x + n.x), fmaf(-dcoef<FAST, 0>(yf, q, L), c.x, fv.x));
+  o.y = fmaf(L.c, (c.x + c.z) + (s.y + n.y), fmaf(-dcoef<FAST, 1>(yf, q, L), c.y, fv.y));
+  o.z = fmaf(L.c, (c.y + c.w) + (s.z + n.z), fmaf(-dcoef<FAST, 2>(yf, q, L), c.z, fv.z));
+  o.w = fmaf(L.c, (c.z + ev) + (s.w + n.w), fmaf(-dcoef<FAST, 3>(yf, q, L), c.w, fv.w));
   return o;
 }
 
@@ -135,59 +165,111 @@ __device__ __forceinline__ float2 avg_pair(const float4& lo, const float4& hi) {
   return make_float2(((lo.x + lo.y) + (hi.x + hi.y)) * 0.25f, ((lo.z + lo.w) + (hi.z + hi.w)) * 0.25f);
 }
 
+// Rows are prefetched kPF iterations before their first use with per-lane 16-byte cp.async copies into
+// a shared-memory ring of kPF rows per warp (u and f), one commit group per row; cells outside the
+// domain are zero-filled by the copy. Row y is taken from the ring once cp.async.wait_group leaves
+// at most kPF-1 newer groups pending.
+constexpr int kPF = 4;  // divides kWin
+
+template <bool UPD>
+struct Ring {
+  float4 u[kPF][32];
+  float4 f[kPF][32];
+};
+template <>
+struct Ring<true> {  // the post-smoothing kernel that also updates a float64 field
+  float4 u[kPF][32];
+  float4 f[kPF][32];
+  double2 w[kPF][2][32];  // float64 solution row, two halves of the lane's 4 cells
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int bytes = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Issue the copies of row y (u only when load_u) into ring slot `slot`, then commit the group.
+template <bool FAST, bool UPD>
+__device__ __forceinline__ void prefetch_row(Ring<UPD>& R, int slot, const float* __restrict__ u,
+                                             const float* __restrict__ f, bool load_u, int y, int ny,
+                                             const StripGeo& g, int nx, const double* __restrict__ w = nullptr,
+                                             int yw = 0) {
+  const int lane = threadIdx.x & 31;
+  const bool valid = FAST || (y >= 0 && y < ny && g.lane_in);
+  const int64_t off = valid ? (int64_t)y * nx + g.xl : 0;
+  if (load_u) cp_async16(&R.u[slot][lane], u + off, valid);
+  cp_async16(&R.f[slot][lane], f + off, valid);
+  if constexpr (UPD) {  // the float64 row yw of the same lane, for the store stage kPF steps later
+    const bool vw = FAST || (yw >= 0 && yw < ny && g.lane_in);
+    const int64_t ow = vw ? (int64_t)yw * nx + g.xl : 0;
+    cp_async16(&R.w[slot][0][lane], w + ow, vw);
+    cp_async16(&R.w[slot][1][lane], w + ow + 2, vw);
+  }
+  cp_async_commit();
+}
+
+// A warp is "interior" when every row its stream touches (including the halo, the rounding of the
+// loop to whole windows and the prefetch distance) lies in 1..ny-2 and its strip in 1..nx-2: then no
+// row or column test is needed and every cell has the interior stencil constants. Interior warps run
+// the FAST instantiation of the body; the others the general one. Both compute the same values.
+__device__ __forceinline__ bool interior(const StripGeo& g, int ystart, int yend, int nx, int ny) {
+  const int ylast = ystart + ((yend - ystart) / kWin + 1) * kWin - 1 + kPF;
+  return ystart >= 1 && ylast <= ny - 2 && g.x0 >= 1 && g.x0 + 32 * 4 - 1 <= nx - 2;
+}
+
 // ------------------------------------------------------------------------------------------------
-// pre-smoothing kernel
+// pre-smoothing
 //   uin  : initial u (ignored when ZERO: the initial guess is 0)
 //   fin  : right-hand side f, or R(r) from the finer level when TAU (f = R(r) + A u is formed here)
 //   fout : TAU only: the formed right-hand side (output rows), for the post-smoothing kernel
 //   uout : u after NS sweeps (output rows)
 //   uc, rc : R(u), R(r) on the next coarser level (nullable: no residual / restriction stage)
 // ------------------------------------------------------------------------------------------------
-template <int NS, bool ZERO, bool TAU>
-__global__ void __launch_bounds__(kThreads) k_pre(const float* __restrict__ uin, const float* __restrict__ fin,
-                                                  float* __restrict__ fout, float* __restrict__ uout,
-                                                  float* __restrict__ uc, float* __restrict__ rc,
-                                                  const __grid_constant__ LevelDesc<float> L, int seg) {
+template <int NS, bool ZERO, bool TAU, bool FAST>
+__device__ __forceinline__ void pre_body(Ring<false>& R, const StripGeo& g, int ystart, int yend,
+                                         const float* __restrict__ uin, const float* __restrict__ fin,
+                                         float* __restrict__ fout, float* __restrict__ uout, float* __restrict__ uc,
+                                         float* __restrict__ rc, const LevelDesc<float>& L) {
   constexpr int NP = 2 * NS;
-  constexpr int LT = TAU ? 1 : 0;        // lag of the tau stage
-  constexpr int LR = NP + 1 + LT;        // lag of the residual stage
+  constexpr int LT = TAU ? 1 : 0;  // lag of the tau stage
+  constexpr int LR = NP + 1 + LT;  // lag of the residual stage
+  constexpr int M = kWin - 1;
   const int nx = L.nx, ny = L.ny;
-  const StripGeo g = strip_geo(nx, ny, seg);
-  if (g.y0 >= ny) return;  // whole warp: surplus warps of the last block
+  const int lane = threadIdx.x & 31;
+  const LaneCoef q = lane_coef(g.xl, L);
   const bool do_res = uc != nullptr;
-  const int ytop = g.y0 - (NP + 1 + LT);            // first row that must be loaded
-  const int ystart = (ytop >= 0 ? ytop : ytop - (kWin - 1)) / kWin * kWin;  // floor to kWin
-  const int yend = g.y1 + (do_res ? LR : NP + LT);  // last pipeline row
-
   float4 U[kWin], F[kWin];
   float4 rprev = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int k = 0; k < kWin; ++k) {
-    U[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    F[k] = U[k];
+    U[k] = rprev;
+    F[k] = rprev;
   }
+#pragma unroll
+  for (int k = 0; k < kPF; ++k) prefetch_row<FAST, false>(R, k, uin, fin, !ZERO, ystart + k, ny, g, nx);
   const int nxc = nx >> 1;
   for (int yb = ystart; yb <= yend; yb += kWin) {
 #pragma unroll
     for (int it = 0; it < kWin; ++it) {
       const int y = yb + it;
-      // ---- load row y
-      {
-        float4 uv = make_float4(0.f, 0.f, 0.f, 0.f), fv = uv;
-        if (y >= 0 && y < ny && g.lane_in) {
-          const int64_t off = (int64_t)y * nx + g.xl;
-          if (!ZERO) uv = ld4(uin, off);
-          fv = ld4(fin, off);
-        }
-        U[it] = uv;
-        F[it] = fv;
-      }
+      // ---- take row y from the ring, prefetch row y + kPF into its slot
+      cp_async_wait<kPF - 1>();
+      U[it] = ZERO ? make_float4(0.f, 0.f, 0.f, 0.f) : R.u[it % kPF][lane];
+      F[it] = R.f[it % kPF][lane];
+      prefetch_row<FAST, false>(R, it % kPF, uin, fin, !ZERO, y + kPF, ny, g, nx);
       // ---- tau: f = R(r) + A u at row y-1 (u still the restricted start)
       if (TAU) {
         const int yt = y - 1;
-        if (yt >= 0 && yt < ny) {
-          const int s = (it - 1) & (kWin - 1);
-          const float4 au = apply_row(U[s], U[(s - 1) & (kWin - 1)], U[(s + 1) & (kWin - 1)], g.xl, yt, L);
+        if (FAST || (yt >= 0 && yt < ny)) {
+          const int s = (it - 1) & M;
+          const float4 au = apply_row<FAST>(U[s], U[(s - 1) & M], U[(s + 1) & M], yt, q, L);
           float4& fr = F[s];
           fr.x = fr.x + au.x;
           fr.y = fr.y + au.y;
@@ -200,28 +282,28 @@ __global__ void __launch_bounds__(kThreads) k_pre(const float* __restrict__ uin,
 #pragma unroll
       for (int t = 1; t <= NP; ++t) {
         const int yp = y - LT - t;
-        if (yp >= 0 && yp < ny) {
-          const int s = (it - LT - t) & (kWin - 1);
+        if (FAST || (yp >= 0 && yp < ny)) {
+          const int s = (it - LT - t) & M;
           // colour 1 (t odd): cells with (x + y) odd, i.e. v = (y+1)&1; colour 0: v = y&1
           const int par = (t & 1) ? ((it - LT - t + 1) & 1) : ((it - LT - t) & 1);
           if (par == 0)
-            phase_row<0>(U[s], U[(s - 1) & (kWin - 1)], U[(s + 1) & (kWin - 1)], F[s], g.xl, yp, L);
+            phase_row<FAST, 0>(U[s], U[(s - 1) & M], U[(s + 1) & M], F[s], yp, q, L, g.lane_in);
           else
-            phase_row<1>(U[s], U[(s - 1) & (kWin - 1)], U[(s + 1) & (kWin - 1)], F[s], g.xl, yp, L);
+            phase_row<FAST, 1>(U[s], U[(s - 1) & M], U[(s + 1) & M], F[s], yp, q, L, g.lane_in);
         }
       }
       // ---- store u, residual and restriction at row y - LR
       {
         const int yr = y - LR;
-        const int s = (it - LR) & (kWin - 1);
-        if (yr >= 0 && yr < ny) {
+        const int s = (it - LR) & M;
+        if (FAST || (yr >= 0 && yr < ny)) {
           if (g.lane_out && yr >= g.y0 && yr < g.y1) st4(uout, (int64_t)yr * nx + g.xl, U[s]);
           if (do_res) {
-            const float4 r = resid_row(U[s], U[(s - 1) & (kWin - 1)], U[(s + 1) & (kWin - 1)], F[s], g.xl, yr, L);
+            const float4 r = resid_row<FAST>(U[s], U[(s - 1) & M], U[(s + 1) & M], F[s], yr, q, L);
             if (((it - LR) & 1) == 1) {  // odd row: the pair (yr-1, yr) is complete
               if (g.lane_out && yr - 1 >= g.y0 && yr < g.y1) {
                 const int64_t coff = (int64_t)(yr >> 1) * nxc + (g.xl >> 1);
-                const float2 cu = avg_pair(U[(s - 1) & (kWin - 1)], U[s]);
+                const float2 cu = avg_pair(U[(s - 1) & M], U[s]);
                 const float2 cr = avg_pair(rprev, r);
                 *reinterpret_cast<float2*>(uc + coff) = cu;
                 *reinterpret_cast<float2*>(rc + coff) = cr;
@@ -233,47 +315,73 @@ __global__ void __launch_bounds__(kThreads) k_pre(const float* __restrict__ uin,
       }
     }
   }
+  cp_async_wait_all();
+}
+
+template <int NS, bool ZERO, bool TAU>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_pre(const float* __restrict__ uin, const float* __restrict__ fin, float* __restrict__ fout,
+          float* __restrict__ uout, float* __restrict__ uc, float* __restrict__ rc,
+          const __grid_constant__ LevelDesc<float> L, int seg) {
+  constexpr int NP = 2 * NS;
+  constexpr int LT = TAU ? 1 : 0;
+  extern __shared__ __align__(16) unsigned char ring_smem[];
+  Ring<false>* rings = reinterpret_cast<Ring<false>*>(ring_smem);
+  const StripGeo g = strip_geo(L.nx, L.ny, seg);
+  if (g.y0 >= L.ny) return;  // whole warp: surplus warps of the last block
+  const int ytop = g.y0 - (NP + 1 + LT);                                    // first row that must be loaded
+  const int ystart = (ytop >= 0 ? ytop : ytop - (kWin - 1)) / kWin * kWin;  // floor to kWin
+  const int yend = g.y1 + (uc != nullptr ? NP + 1 + LT : NP + LT);         // last pipeline row
+  Ring<false>& R = rings[threadIdx.x >> 5];
+  if (interior(g, ystart, yend, L.nx, L.ny))
+    pre_body<NS, ZERO, TAU, true>(R, g, ystart, yend, uin, fin, fout, uout, uc, rc, L);
+  else
+    pre_body<NS, ZERO, TAU, false>(R, g, ystart, yend, uin, fin, fout, uout, uc, rc, L);
 }
 
 // ------------------------------------------------------------------------------------------------
-// post-smoothing kernel: uout = S^NS(uin + P(uc - R(uin)))
+// post-smoothing: uout = S^NS(uin + P(uc - R(uin)))
 // ------------------------------------------------------------------------------------------------
-template <int NS>
-__global__ void __launch_bounds__(kThreads) k_post(const float* __restrict__ uin, const float* __restrict__ f,
-                                                   const float* __restrict__ uc, float* __restrict__ uout,
-                                                   const __grid_constant__ LevelDesc<float> L, int seg) {
+template <int NS, bool FAST, bool UPD>
+__device__ __forceinline__ void post_body(Ring<UPD>& R, const StripGeo& g, int ystart, int yend,
+                                          const float* __restrict__ uin, const float* __restrict__ f,
+                                          const float* __restrict__ uc, float* __restrict__ uout,
+                                          double* __restrict__ u64, const LevelDesc<float>& L) {
   constexpr int NP = 2 * NS;
   constexpr int LW = NP + 1;  // lag of the store stage; phase t runs at row y - 1 - t
+  constexpr int M = kWin - 1;
   const int nx = L.nx, ny = L.ny;
-  const StripGeo g = strip_geo(nx, ny, seg);
-  if (g.y0 >= ny) return;
-  const int ytop = g.y0 - NP;  // even, so correction pairs stay aligned
-  const int ystart = (ytop >= 0 ? ytop : ytop - (kWin - 1)) / kWin * kWin;
-  const int yend = g.y1 + LW;
+  const int lane = threadIdx.x & 31;
+  const LaneCoef q = lane_coef(g.xl, L);
   float4 U[kWin], F[kWin];
 #pragma unroll
   for (int k = 0; k < kWin; ++k) {
     U[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     F[k] = U[k];
   }
+#pragma unroll
+  for (int k = 0; k < kPF; ++k)
+    prefetch_row<FAST, UPD>(R, k, uin, f, true, ystart + k, ny, g, nx, u64, ystart + k - LW);
   const int nxc = nx >> 1;
   for (int yb = ystart; yb <= yend; yb += kWin) {
 #pragma unroll
     for (int it = 0; it < kWin; ++it) {
       const int y = yb + it;
-      {
-        float4 uv = make_float4(0.f, 0.f, 0.f, 0.f), fv = uv;
-        if (y >= 0 && y < ny && g.lane_in) {
-          const int64_t off = (int64_t)y * nx + g.xl;
-          uv = ld4(uin, off);
-          fv = ld4(f, off);
-        }
-        U[it] = uv;
-        F[it] = fv;
+      cp_async_wait<kPF - 1>();
+      U[it] = R.u[it % kPF][lane];
+      F[it] = R.f[it % kPF][lane];
+      // UPD: the float64 solution row stored at the end of this step (row y - LW)
+      double2 ua = make_double2(0.0, 0.0), ub = ua;
+      if constexpr (UPD) {
+        ua = R.w[it % kPF][0][lane];
+        ub = R.w[it % kPF][1][lane];
       }
+      prefetch_row<FAST, UPD>(R, it % kPF, uin, f, true, y + kPF, ny, g, nx, u64, y + kPF - LW);
+      const int yw = y - LW;
+      const bool wr = yw >= g.y0 && yw < g.y1 && g.lane_out;
       // coarse-grid correction of the row pair (y-1, y)
-      if ((it & 1) == 1 && y < ny && y >= 1 && g.lane_in) {
-        float4& lo = U[(it - 1) & (kWin - 1)];
+      if ((it & 1) == 1 && (FAST || (y < ny && y >= 1 && g.lane_in))) {
+        float4& lo = U[(it - 1) & M];
         float4& hi = U[it];
         const float2 cv = *reinterpret_cast<const float2*>(uc + (int64_t)(y >> 1) * nxc + (g.xl >> 1));
         const float2 ru = avg_pair(lo, hi);
@@ -290,22 +398,52 @@ __global__ void __launch_bounds__(kThreads) k_post(const float* __restrict__ uin
 #pragma unroll
       for (int t = 1; t <= NP; ++t) {
         const int yp = y - 1 - t;
-        if (yp >= 0 && yp < ny) {
-          const int s = (it - 1 - t) & (kWin - 1);
+        if (FAST || (yp >= 0 && yp < ny)) {
+          const int s = (it - 1 - t) & M;
           const int par = (t & 1) ? ((it - 1 - t + 1) & 1) : ((it - 1 - t) & 1);
           if (par == 0)
-            phase_row<0>(U[s], U[(s - 1) & (kWin - 1)], U[(s + 1) & (kWin - 1)], F[s], g.xl, yp, L);
+            phase_row<FAST, 0>(U[s], U[(s - 1) & M], U[(s + 1) & M], F[s], yp, q, L, g.lane_in);
           else
-            phase_row<1>(U[s], U[(s - 1) & (kWin - 1)], U[(s + 1) & (kWin - 1)], F[s], g.xl, yp, L);
+            phase_row<FAST, 1>(U[s], U[(s - 1) & M], U[(s + 1) & M], F[s], yp, q, L, g.lane_in);
         }
       }
-      {
-        const int yw = y - LW;
-        const int s = (it - LW) & (kWin - 1);
-        if (yw >= g.y0 && yw < g.y1 && g.lane_out) st4(uout, (int64_t)yw * nx + g.xl, U[s]);
+      if (wr) {
+        const float4 e = U[(it - LW) & M];
+        if (UPD) {  // mixed precision: u64 += e, the float64 update of the refinement step
+          double2* dst = reinterpret_cast<double2*>(u64 + (int64_t)yw * nx + g.xl);
+          ua.x += (double)e.x;
+          ua.y += (double)e.y;
+          ub.x += (double)e.z;
+          ub.y += (double)e.w;
+          dst[0] = ua;
+          dst[1] = ub;
+        } else {
+          st4(uout, (int64_t)yw * nx + g.xl, e);
+        }
       }
     }
   }
+  cp_async_wait_all();
+}
+
+template <int NS, bool UPD>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_post(const float* __restrict__ uin, const float* __restrict__ f, const float* __restrict__ uc,
+           float* __restrict__ uout, double* __restrict__ u64, const __grid_constant__ LevelDesc<float> L,
+           int seg) {
+  constexpr int NP = 2 * NS;
+  extern __shared__ __align__(16) unsigned char ring_smem[];
+  Ring<UPD>* rings = reinterpret_cast<Ring<UPD>*>(ring_smem);
+  const StripGeo g = strip_geo(L.nx, L.ny, seg);
+  if (g.y0 >= L.ny) return;
+  const int ytop = g.y0 - NP;  // even, so correction pairs stay aligned
+  const int ystart = (ytop >= 0 ? ytop : ytop - (kWin - 1)) / kWin * kWin;
+  const int yend = g.y1 + NP + 1;
+  Ring<UPD>& R = rings[threadIdx.x >> 5];
+  if (interior(g, ystart, yend, L.nx, L.ny))
+    post_body<NS, true, UPD>(R, g, ystart, yend, uin, f, uc, uout, u64, L);
+  else
+    post_body<NS, false, UPD>(R, g, ystart, yend, uin, f, uc, uout, u64, L);
 }
 
 int blocks_for(int nx, int ny, int seg) {
@@ -322,7 +460,8 @@ bool stream2d_supported(int nx, int ny, int nu) {
 }
 
 #define PRE_CASE(NSV, Z, T)                                                                      \
-  k_pre<NSV, Z, T><<<blocks_for(L.nx, L.ny, seg), kThreads, 0, stream>>>(uin, fin, fout, uout, uc, rc, L, seg)
+  k_pre<NSV, Z, T><<<blocks_for(L.nx, L.ny, seg), kThreads, sizeof(Ring<false>) * kWarps, stream>>>( \
+      uin, fin, fout, uout, uc, rc, L, seg)
 
 cudaError_t launch_stream2d_pre(const float* uin, const float* fin, float* fout, float* uout, float* uc, float* rc,
                                 const LevelDesc<float>& L, int nu, bool zero_init, bool tau, int seg,
@@ -345,15 +484,29 @@ cudaError_t launch_stream2d_pre(const float* uin, const float* fin, float* fout,
   return cudaGetLastError();
 }
 
-cudaError_t launch_stream2d_post(const float* uin, const float* f, const float* uc, float* uout,
+template <int NS, bool UPD>
+cudaError_t post_launch(const float* uin, const float* f, const float* uc, float* uout, double* u64,
+                        const LevelDesc<float>& L, int seg, cudaStream_t stream) {
+  constexpr size_t smem = sizeof(Ring<UPD>) * kWarps;
+  static bool attr = false;  // > 48 KB of dynamic shared memory needs the opt-in, once per kernel
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_post<NS, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_post<NS, UPD><<<blocks_for(L.nx, L.ny, seg), kThreads, smem, stream>>>(uin, f, uc, uout, u64, L, seg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream2d_post(const float* uin, const float* f, const float* uc, float* uout, double* u64,
                                  const LevelDesc<float>& L, int nu, int seg, cudaStream_t stream) {
-  const int b = blocks_for(L.nx, L.ny, seg);
-  switch (nu) {
-    case 1: k_post<1><<<b, kThreads, 0, stream>>>(uin, f, uc, uout, L, seg); break;
-    case 2: k_post<2><<<b, kThreads, 0, stream>>>(uin, f, uc, uout, L, seg); break;
+  switch (nu * 2 + (u64 != nullptr)) {
+    case 2: return post_launch<1, false>(uin, f, uc, uout, u64, L, seg, stream);
+    case 3: return post_launch<1, true>(uin, f, uc, uout, u64, L, seg, stream);
+    case 4: return post_launch<2, false>(uin, f, uc, uout, u64, L, seg, stream);
+    case 5: return post_launch<2, true>(uin, f, uc, uout, u64, L, seg, stream);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace fasmg

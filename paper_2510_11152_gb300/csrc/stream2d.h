@@ -19,8 +19,9 @@ cudaError_t launch_stream2d_pre(const float* uin, const float* fin, float* fout,
                                 const LevelDesc<float>& L, int nu, bool zero_init, bool tau, int seg,
                                 cudaStream_t stream);
 
-// Post-smoothing: uout = S^nu(uin + P(uc - R(uin))).
-cudaError_t launch_stream2d_post(const float* uin, const float* f, const float* uc, float* uout,
+// Post-smoothing: e = S^nu(uin + P(uc - R(uin))); uout = e, or, when u64 is not null, u64 += e in
+// float64 (the update of a mixed-precision refinement step) and uout is not written.
+cudaError_t launch_stream2d_post(const float* uin, const float* f, const float* uc, float* uout, double* u64,
                                  const LevelDesc<float>& L, int nu, int seg, cudaStream_t stream);
 
 }  // namespace fasmg

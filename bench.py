@@ -108,6 +108,29 @@ class Clocks:
                 "samples": len(sm), "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
 
 
+def traffic_table():
+    """DRAM bytes per cell from the committed ncu summaries, valid only while the kernel sources are
+    unchanged (profiles/traffic.json)."""
+    import hashlib
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return {}
+    out = {}
+    for key, v in t.items():
+        if not isinstance(v, dict):
+            continue
+        m = hashlib.sha256()
+        try:
+            for f in v["sources"]:
+                m.update(open(os.path.join(ROOT, f), "rb").read())
+        except OSError:
+            continue
+        if m.hexdigest()[:16] == v["hash"]:
+            out[key] = v["bytes_per_cell"]
+    return out
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -132,8 +155,8 @@ def kernel_work(family, level, inner_first_zero=True):
         return "hbm", 3.25 * b, "B"
     if family == "ir":  # r = b - A u: 3 DADD + 2 DFMA per cell
         return "alu", 7.0, "FLOP"
-    if family == "update":  # u += e: read u, e, write u
-        return "hbm", 20.0, "B"
+    if family == "update":  # fused post-smoothing + u += e: u, f, u_c in (float32), float64 u in/out
+        return "hbm", 3.0 * b + 1.0 + 16.0, "B"
     return None, None, None
 
 
@@ -271,6 +294,10 @@ def run_ours(args, ws, rank, local):
 
     roof = roofline_of(dom) or {"bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s",
                                 "frac": None, "traffic": None}
+    tt = traffic_table().get("%s@%d" % (dom["family"], dom["level"]))
+    if tt is not None:
+        roof["traffic"] = tt * dom["units"] / dom["launches"]
+        roof["traffic_source"] = "ncu dram bytes per cell (profiles/traffic.json) x cells per launch"
     roof.update({"kernel": "%s@level%d" % (dom["family"], dom["level"]),
                  "share_of_kernel_time": dom["ms"] / total_ms if total_ms else None,
                  "ms_per_launch": dom["ms"] / dom["launches"]})

@@ -149,7 +149,7 @@ typedef enum {
   FAS_K_IR = 6,          /* mixed precision: float64 residual r = b - A u, rounded to float32    */
   FAS_K_NORM = 7,        /* norms and means                                                     */
   FAS_K_OTHER = 8,       /* right-hand sides, fills, conversions                                */
-  FAS_K_UPDATE = 9,      /* mixed precision: float64 u += e                                      */
+  FAS_K_UPDATE = 9,      /* mixed precision: float64 u += e (alone or fused into the post-smoothing) */
   FAS_K_NFAMILIES = 10
 } fas_kernel_family;
 

@@ -529,7 +529,8 @@ fas_status vcycle_fast(fas_ctx* c, Hier<float>& H, bool zero_init, double* u64) 
   for (int l = nf - 1; l >= 0; --l) {
     const LevelDesc<float>& L = H.desc[l];
     const int seg = seg_for_level(c, L.nx, L.ny);
-    Prof pr(c, FAS_K_PROLONG, l, (double)c->shape[l].cells());
+    // the level-0 launch that also adds the result to the float64 solution is timed as an update
+    Prof pr(c, (l == 0 && u64) ? FAS_K_UPDATE : FAS_K_PROLONG, l, (double)c->shape[l].cells());
     cudaError_t e = launch_stream2d_post(H.u2[l], H.f[l], H.u[l + 1], H.u[l], l == 0 ? u64 : nullptr, L, p.nu2, seg,
                                          c->stream);
     if (e != cudaSuccess) return fail(FAS_ECUDA, std::string("stream2d post: ") + cudaGetErrorString(e));

@@ -168,6 +168,32 @@ fas_status fas_prof_enable(fas_ctx* ctx, int on);
  * (family, level) pairs seen (may exceed cap). */
 fas_status fas_prof_read(fas_ctx* ctx, fas_prof_record* out, int cap, int* count);
 
+/* --- solving without allocating ---------------------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot allocate
+ * device memory when they need a solve: code running while a stream is captured into a CUDA graph,
+ * programs whose allocator has reserved all device memory up front, host callbacks (where allocating
+ * CUDA calls are forbidden) and real-time loops that cannot take an allocation's latency or failure.
+ *
+ * fas_vcycle_small_static runs ncycles V-cycles (the V-cycle of fas_vcycle, float64, constant kappa,
+ * coarsest level smoothed) on device field u in place, for right-hand side f, with no context and no
+ * allocation: the whole level hierarchy is held in one CTA's shared memory, and the only global
+ * scratch -- the level descriptors and the residual-norm slot, about 26 KB -- is a static device
+ * array that every GPU loading the library keeps until the process exits.
+ *   p         problem and smoothing parameters as for fas_create (kappa must be NULL, coarse_exact 0,
+ *             precision FAS_FP64; kmax, tol, inner_cycles, use_graph, path, seg_rows are ignored)
+ *   u, f      DEVICE pointers of the caller, dense C order (x fastest), nx*ny(*nz) float64 each
+ *   res_host  HOST pointer (may be NULL) receiving ||f - A u||_2 after the last cycle; when given,
+ *             the call waits for the stream, otherwise it returns with the work enqueued
+ *   stream    cudaStream_t (NULL: legacy default stream)
+ * Limits: at most 16 levels and a hierarchy (u and f on every level, the restricted start below the
+ * top, plus descriptors) of at most 200 KB of shared memory: float64 grids up to 64 x 64 in 2D or
+ * 16 x 16 x 16 in 3D. Larger grids return FAS_EINVAL with the needed size in fas_last_error().
+ * The first call on a device looks up the static array's device address; make that first call before
+ * any stream capture begins. All calls share the array, so calls that overlap on the GPU race; the
+ * caller must serialise them (one stream, or events). */
+fas_status fas_vcycle_small_static(const fas_params* p, double* u, const double* f, int ncycles,
+                                   double* res_host, void* stream);
+
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char* fas_last_error(void);
 

@@ -22,7 +22,7 @@ __all__ = [
     "FasError", "fas_params", "fas_info", "load", "fas_default_params", "fas_create", "fas_destroy",
     "fas_num_levels", "fas_vcycle", "fas_solve", "fas_heat_run", "fas_heat_run_host", "fas_residual",
     "fas_smooth", "fas_restrict", "fas_prolong_add", "fas_last_error", "fas_launch_count", "Solver",
-    "fas_prof_enable", "fas_prof_read", "make_params",
+    "fas_prof_enable", "fas_prof_read", "make_params", "fas_vcycle_small_static",
 ]
 
 FAS_OK, FAS_EINVAL, FAS_ENOMEM, FAS_ENOTCONV, FAS_ENONFINITE, FAS_ETIMEOUT, FAS_ECUDA, FAS_EUNSUPPORTED = range(8)
@@ -90,6 +90,7 @@ def load(path: str | None = None):
         "fas_last_error": (ctypes.c_char_p, []),
         "fas_launch_count": (ctypes.c_longlong, [_P, _I]),
         "fas_prof_enable": (_I, [_P, _I]),
+        "fas_vcycle_small_static": (_I, [ctypes.POINTER(fas_params), _P, _P, _I, ctypes.POINTER(_D), _P]),
         "fas_prof_read": (_I, [_P, ctypes.c_void_p, _I, ctypes.POINTER(_I)]),
     }
     for name, (res, args) in sig.items():
@@ -243,6 +244,17 @@ def fas_restrict(ctx: _Ctx, level: int, u, uc) -> None:
 def fas_prolong_add(ctx: _Ctx, level: int, u, c) -> None:
     _check(load().fas_prolong_add(ctx.handle, level, _dev(u, "u", ctx.level_cells(level)),
                                   _dev(c, "c", ctx.level_cells(level + 1))), "fas_prolong_add")
+
+
+def fas_vcycle_small_static(params: fas_params, u, f, ncycles: int, stream=None, want_res: bool = True):
+    """ncycles V-cycles on a small grid with no device allocation (see include/fas.h); returns
+    ||f - A u||_2 after the last cycle (None when want_res is False: the call does not wait)."""
+    n = params.n[0] * params.n[1] * (params.n[2] if params.dim == 3 else 1)
+    res = _D()
+    st = load().fas_vcycle_small_static(ctypes.byref(params), _dev(u, "u", n), _dev(f, "f", n), int(ncycles),
+                                        ctypes.byref(res) if want_res else None, _stream_handle(stream))
+    _check(st, "fas_vcycle_small_static")
+    return res.value if want_res else None
 
 
 def fas_launch_count(ctx: _Ctx, reset: bool = False) -> int:

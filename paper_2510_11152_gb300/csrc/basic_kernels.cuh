@@ -141,7 +141,7 @@ __global__ void k_residual(T* r, const T* u, const T* f, LevelDesc<T> L, float n
 }
 
 // out[0] = sqrt(sum of partials) / nscale, summed in a fixed order by one block.
-__global__ void k_finish_norm(const double* partials, int nblocks, double* out, double inv_scale) {
+static __global__ void k_finish_norm(const double* partials, int nblocks, double* out, double inv_scale) {
   double v = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[b];
   v = block_sum(v);
@@ -149,7 +149,7 @@ __global__ void k_finish_norm(const double* partials, int nblocks, double* out, 
 }
 
 // out[0] = sum of partials (no square root), used for means.
-__global__ void k_finish_sum(const double* partials, int nblocks, double* out) {
+static __global__ void k_finish_sum(const double* partials, int nblocks, double* out) {
   double v = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[b];
   v = block_sum(v);
@@ -189,7 +189,7 @@ __global__ void k_sub_mean(T* x, const T* y, int64_t n, const double* sum) {
 
 // heat step right-hand side: b = u + dt * fsrc (fsrc may be null: b = u), with the per-block partial
 // sums of b^2 (float squares) for ||b||
-__global__ void k_heat_rhs(double* b, const double* u, const double* fsrc, double dt, int64_t n, double* partials) {
+static __global__ void k_heat_rhs(double* b, const double* u, const double* fsrc, double dt, int64_t n, double* partials) {
   float acc = 0.f;
   for (int64_t i = gtid(); i < n; i += gstride()) {
     const double v = fsrc ? fma(dt, fsrc[i], u[i]) : u[i];
@@ -202,7 +202,7 @@ __global__ void k_heat_rhs(double* b, const double* u, const double* fsrc, doubl
 }
 
 // ---- mixed precision (iterative refinement): u += e, and r32 = (float)(b - A u) with its norm
-__global__ void k_ir_update(double* u, const float* e, int64_t n) {
+static __global__ void k_ir_update(double* u, const float* e, int64_t n) {
   for (int64_t i = gtid(); i < n; i += gstride()) u[i] += (double)e[i];
 }
 

@@ -34,6 +34,9 @@ struct Hier {
   bool allocated = false;
 };
 
+// Record the message fas_last_error() returns on this thread.
+void set_last_error(const std::string& msg);
+
 struct LevelShape {
   int nx, ny, nz;
   double h;

@@ -727,6 +727,8 @@ fas_status check_level(const fas_ctx* c, int level, bool needs_coarser) {
 
 }  // namespace
 
+void fasmg::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 // =============================================================================================
 // C ABI
 // =============================================================================================

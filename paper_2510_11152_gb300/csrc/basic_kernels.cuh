@@ -33,6 +33,7 @@ __device__ __forceinline__ void smooth_colour_range(T* u, const T* f, const Leve
 template <typename T, int DIM>
 __device__ __forceinline__ float residual_range(T* r, const T* u, const T* f, const LevelDesc<T>& L,
                                                 float nscale, int64_t t0, int64_t stride) {
+  // nscale: power-of-two factor applied before squaring (keeps float squares in range)
   const int64_t n = (int64_t)L.nx * L.ny * L.nz;
   float acc = 0.f;
   for (int64_t idx = t0; idx < n; idx += stride) {
@@ -132,20 +133,20 @@ __global__ void k_smooth_colour(T* u, const T* f, LevelDesc<T> L, int colour) {
   smooth_colour_range<T, DIM>(u, f, L, colour, gtid(), gstride());
 }
 
-// r (nullable) = f - A u; per-block partial of sum (nscale r)^2 into partials[blockIdx.x].
+// r (nullable) = f - A u; per-block partial of sum (s r)^2 into partials[blockIdx.x], s = *nsp (or 1).
 template <typename T, int DIM>
-__global__ void k_residual(T* r, const T* u, const T* f, LevelDesc<T> L, float nscale, double* partials) {
-  const float acc = residual_range<T, DIM>(r, u, f, L, nscale, gtid(), gstride());
+__global__ void k_residual(T* r, const T* u, const T* f, LevelDesc<T> L, const float* nsp, double* partials) {
+  const float acc = residual_range<T, DIM>(r, u, f, L, nsp ? *nsp : 1.f, gtid(), gstride());
   const double s = block_sum((double)acc);
   if (threadIdx.x == 0 && partials) partials[blockIdx.x] = s;
 }
 
-// out[0] = sqrt(sum of partials) / nscale, summed in a fixed order by one block.
-static __global__ void k_finish_norm(const double* partials, int nblocks, double* out, double inv_scale) {
+// out[0] = sqrt(sum of partials) / s (s = *nsp, or 1), summed in a fixed order by one block.
+static __global__ void k_finish_norm(const double* partials, int nblocks, double* out, const float* nsp) {
   double v = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[b];
   v = block_sum(v);
-  if (threadIdx.x == 0) out[0] = sqrt(v) * inv_scale;
+  if (threadIdx.x == 0) out[0] = sqrt(v) / (nsp ? (double)*nsp : 1.0);
 }
 
 // out[0] = sum of partials (no square root), used for means.
@@ -207,9 +208,10 @@ static __global__ void k_ir_update(double* u, const float* e, int64_t n) {
 }
 
 template <int DIM>
-__global__ void k_ir_residual(float* r32, const double* u, const double* b, LevelDesc<double> L, float nscale,
+__global__ void k_ir_residual(float* r32, const double* u, const double* b, LevelDesc<double> L, const float* nsp,
                               double* partials) {
   const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+  const float nscale = nsp ? *nsp : 1.f;
   float acc = 0.f;
   for (int64_t idx = gtid(); idx < n; idx += gstride()) {
     const int i = (int)(idx & (L.nx - 1));
@@ -227,7 +229,8 @@ __global__ void k_ir_residual(float* r32, const double* u, const double* b, Leve
 // per-block partial of sum (nscale x)^2, squares of the float-rounded values (norms for stopping
 // tests need a few digits only, and the conversion keeps the work off the FP64 pipe)
 template <typename T>
-__global__ void k_norm2(const T* x, int64_t n, float nscale, double* partials) {
+__global__ void k_norm2(const T* x, int64_t n, const float* nsp, double* partials) {
+  const float nscale = nsp ? *nsp : 1.f;
   float acc = 0.f;
   for (int64_t i = gtid(); i < n; i += gstride()) {
     const float v = (float)x[i] * nscale;
@@ -427,6 +430,67 @@ __global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayou
     const int64_t n = (int64_t)L.nx * L.ny * L.nz;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) utop[i] = sm[S.off_u[A.l0] + i];
   }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Device-side state of one solve (Algorithm 1's outer loop): the stopping decision is taken on the
+// device, so that the same kernels serve a host-driven loop and a graph with a conditional node.
+// ------------------------------------------------------------------------------------------------
+struct SolveState {
+  double fn;      // ||f||_2
+  double res0;    // ||f - A u||_2 before the first cycle
+  double res;     // after the last cycle
+  double ref;     // reference of the relative test (||f||, or res0 when f = 0), 1 in absolute mode
+  double w;       // 1 (relative test) or h^{d/2} (the paper's absolute h-weighted norm)
+  double tol;
+  float nscale;   // power of two applied to values before squaring them in float
+  int kmax;
+  int cycles;
+  int converged;
+  int nonfinite;
+  int cond;       // 1: run another cycle
+};
+
+// After ||f|| is known: the norm scale (a power of two bringing the rms of f near 1).
+static __global__ void k_solve_begin(SolveState* S, double tol, int kmax, double w, double ncells) {
+  const double fn = S->fn;
+  float s = 1.f;
+  if (fn > 0.0 && isfinite(fn)) {
+    const int e = (int)lrint(log2(fn / sqrt(ncells)));
+    s = (float)ldexp(1.0, -max(-120, min(120, e)));
+  }
+  S->nscale = s;
+  S->tol = tol;
+  S->kmax = kmax;
+  S->w = w;
+  S->cycles = 0;
+  S->converged = 0;
+  S->nonfinite = 0;
+  S->cond = 1;  // Algorithm 1 runs at least one cycle
+}
+
+// After the initial residual: the reference of the relative test.
+static __global__ void k_solve_ref(SolveState* S, int relative) {
+  S->ref = relative ? (S->fn > 0.0 ? S->fn : S->res0) : 1.0;
+}
+
+// After each cycle's residual norm (in S->res): count it and decide whether to continue. When
+// set_cond, also set the graph's conditional (the kernel then runs inside the while node's body).
+static __global__ void k_solve_step(SolveState* S, cudaGraphConditionalHandle h, int set_cond) {
+  S->cycles += 1;
+  const double res = S->w * S->res;
+  int cond = 1;
+  if (!isfinite(res)) {
+    S->nonfinite = 1;
+    cond = 0;
+  } else if (res <= S->tol * S->ref) {
+    S->converged = 1;
+    cond = 0;
+  } else if (S->cycles >= S->kmax) {
+    cond = 0;
+  }
+  S->cond = cond;
+  if (set_cond) cudaGraphSetConditional(h, (unsigned)cond);
 }
 
 }  // namespace fasmg

@@ -45,6 +45,18 @@ struct LevelShape {
 
 }  // namespace fasmg
 
+// A captured solve: prologue, then a while node whose body is one cycle (see fas_api.cu).
+struct SolveGraph {
+  double* u = nullptr;
+  const double* f = nullptr;
+  const double* fsrc = nullptr;
+  double dt = 0.0;
+  int kind = 0;  // 0 solve, 1 heat step (forms b = u + dt fsrc first)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long n_pro = 0, n_body = 0;  // kernel launches of the prologue and of one body pass
+};
+
 struct ProfSpan {
   cudaEvent_t beg, end;
   int family, level;
@@ -69,6 +81,12 @@ struct fas_ctx {
   double* host_u = nullptr;    // device buffers of fas_heat_run_host
   double* host_f = nullptr;
   long long launches = 0;
+  fasmg::SolveState* S = nullptr;   // device state of the current solve
+  fasmg::SolveState* Sh = nullptr;  // pinned host mirror
+  cudaStream_t side = nullptr;      // captures a solve graph's prologue
+  cudaStream_t side2 = nullptr;     // captures the while node's body
+  std::vector<SolveGraph> graphs;
+  bool capturing = false;
   // kernel timing
   bool prof = false;
   std::vector<ProfSpan> spans;

@@ -72,7 +72,7 @@ struct Prof {
   fas_ctx* c;
   ProfSpan span;
   bool on;
-  Prof(fas_ctx* ctx, int family, int level, double units) : c(ctx), on(ctx->prof) {
+  Prof(fas_ctx* ctx, int family, int level, double units) : c(ctx), on(ctx->prof && !ctx->capturing) {
     c->launches += 1;
     if (!on) return;
     span.beg = pool_event(c);
@@ -409,17 +409,18 @@ void launch_smooth(fas_ctx* c, const LevelDesc<T>& L, int level, T* u, const T* 
   }
 }
 
-// ||f - A u||_2 into c->d_scalar[0]; r (nullable) receives the residual.
+// ||f - A u||_2 into *out (device); r (nullable) receives the residual; nsp: device norm scale or null.
 template <typename T, int DIM>
-void launch_residual(fas_ctx* c, const LevelDesc<T>& L, int level, T* r, const T* u, const T* f, float nscale) {
+void launch_residual(fas_ctx* c, const LevelDesc<T>& L, int level, T* r, const T* u, const T* f, const float* nsp,
+                     double* out) {
   const int64_t n = (int64_t)L.nx * L.ny * L.nz;
   const int g = grid_for(c, n);
   {
     Prof pr(c, FAS_K_RESIDUAL, level, (double)n);
-    k_residual<T, DIM><<<g, kBlock, 0, c->stream>>>(r, u, f, L, nscale, c->partials);
+    k_residual<T, DIM><<<g, kBlock, 0, c->stream>>>(r, u, f, L, nsp, c->partials);
   }
   Prof pr(c, FAS_K_NORM, level, 0.0);
-  k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0 / nscale);
+  k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, out, nsp);
 }
 
 template <typename T, int DIM>
@@ -438,11 +439,6 @@ fas_status launch_coarse(fas_ctx* c, Hier<T>& H, int l0, T* utop, const T* ftop)
   A.nu1 = p.nu1;
   A.nu2 = p.nu2;
   A.nuc = p.nu_coarse > 0 ? p.nu_coarse : p.nu1;
-  static bool attr_set = false;  // per template instantiation
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_coarse_smem<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseSmemLimit);
-    attr_set = true;
-  }
   Prof pr(c, FAS_K_COARSE, l0, (double)c->shape[l0].cells());
   k_coarse_smem<T, DIM><<<1, kCoarseThreads, H.smem_bytes, c->stream>>>(A, H.smem, utop, ftop);
   return FAS_OK;
@@ -462,7 +458,7 @@ fas_status vcycle_basic_from(fas_ctx* c, Hier<T>& H, int lfrom, T* utop, const T
     const int64_t n = (int64_t)L.nx * L.ny * L.nz;
     {
       Prof pr(c, FAS_K_RESIDUAL, l, (double)n);
-      k_residual<T, DIM><<<grid_for(c, n), kBlock, 0, c->stream>>>(H.r[l], u, f, L, 1.f, nullptr);
+      k_residual<T, DIM><<<grid_for(c, n), kBlock, 0, c->stream>>>(H.r[l], u, f, L, nullptr, nullptr);
     }
     const int64_t nc = n >> DIM;
     {
@@ -552,56 +548,46 @@ fas_status sync_read(fas_ctx* c, double* out) {
   return FAS_OK;
 }
 
-// ||x||_2 of a float64 field of level-0 size (squares of the float-rounded values, scaled by nscale)
-fas_status norm_of(fas_ctx* c, const double* x, float nscale, double* out) {
+// ---------------------------------------------------------------------------------------------
+// norms and the solve loop (Algorithm 1's outer loop). The stopping decision is computed on the
+// device (SolveState); the host loop reads it after each cycle, the graph's while node reads it
+// through its conditional handle.
+// ---------------------------------------------------------------------------------------------
+
+// ||x||_2 of a float64 level-0 field into *out (device), squares of the float-rounded values
+void enqueue_norm(fas_ctx* c, const double* x, const float* nsp, double* out) {
   const int64_t n = c->shape[0].cells();
   const int g = grid_for(c, n);
   {
     Prof pr(c, FAS_K_NORM, 0, (double)n);
-    k_norm2<double><<<g, kBlock, 0, c->stream>>>(x, n, nscale, c->partials);
+    k_norm2<double><<<g, kBlock, 0, c->stream>>>(x, n, nsp, c->partials);
   }
-  {
+  Prof pr(c, FAS_K_NORM, 0, 0.0);
+  k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, out, nsp);
+}
+
+// ||b - A u||_2 into *out; mixed precision also leaves r32 = (float)(b - A u) in h32.f[0]
+void enqueue_residual_norm(fas_ctx* c, const double* u, const double* b, const float* nsp, double* out) {
+  if (c->p.precision == FAS_MIXED) {
+    const int64_t n = c->shape[0].cells();
+    const int g = grid_for(c, n);
+    {
+      Prof pr(c, FAS_K_IR, 0, (double)n);
+      if (c->p.dim == 2)
+        k_ir_residual<2><<<g, kBlock, 0, c->stream>>>(c->h32.f[0], u, b, c->h64.desc[0], nsp, c->partials);
+      else
+        k_ir_residual<3><<<g, kBlock, 0, c->stream>>>(c->h32.f[0], u, b, c->h64.desc[0], nsp, c->partials);
+    }
     Prof pr(c, FAS_K_NORM, 0, 0.0);
-    k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0 / nscale);
+    k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, out, nsp);
+  } else if (c->p.dim == 2) {
+    launch_residual<double, 2>(c, c->h64.desc[0], 0, nullptr, u, b, nsp, out);
+  } else {
+    launch_residual<double, 3>(c, c->h64.desc[0], 0, nullptr, u, b, nsp, out);
   }
-  return sync_read(c, out);
 }
 
-float pick_scale(double norm, int64_t n) {
-  // power of two bringing the rms value near 1 so that float squares neither under- nor overflow
-  if (!(norm > 0.0) || !std::isfinite(norm)) return 1.f;
-  const double rms = norm / std::sqrt((double)n);
-  const int e = (int)std::lround(std::log2(rms));
-  return (float)std::ldexp(1.0, -std::max(-120, std::min(120, e)));
-}
-
-template <int DIM>
-fas_status residual64(fas_ctx* c, const double* u, const double* f, float nscale, double* out) {
-  launch_residual<double, DIM>(c, c->h64.desc[0], 0, nullptr, u, f, nscale);
-  return sync_read(c, out);
-}
-
-fas_status residual_norm64(fas_ctx* c, const double* u, const double* f, float nscale, double* out) {
-  return c->p.dim == 2 ? residual64<2>(c, u, f, nscale, out) : residual64<3>(c, u, f, nscale, out);
-}
-
-// mixed: r32 = (float)(b - A u), returns ||b - A u||
-template <int DIM>
-fas_status ir_residual(fas_ctx* c, const double* u, const double* b, float nscale, double* out) {
-  const int64_t n = c->shape[0].cells();
-  const int g = grid_for(c, n);
-  {
-    Prof pr(c, FAS_K_IR, 0, (double)n);
-    k_ir_residual<DIM><<<g, kBlock, 0, c->stream>>>(c->h32.f[0], u, b, c->h64.desc[0], nscale, c->partials);
-  }
-  {
-    Prof pr(c, FAS_K_NORM, 0, 0.0);
-    k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0 / nscale);
-  }
-  return sync_read(c, out);
-}
-
-fas_status remove_mean(fas_ctx* c, double* x, const double* y) {
+void enqueue_remove_mean(fas_ctx* c, double* x, const double* y) {
   const int64_t n = c->shape[0].cells();
   const int g = grid_for(c, n);
   {
@@ -612,17 +598,8 @@ fas_status remove_mean(fas_ctx* c, double* x, const double* y) {
     Prof pr(c, FAS_K_NORM, 0, 0.0);
     k_finish_sum<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar + 1);
   }
-  {
-    Prof pr(c, FAS_K_OTHER, 0, (double)n);
-    k_sub_mean<double><<<g, kBlock, 0, c->stream>>>(x, y, n, c->d_scalar + 1);
-  }
-  CUDA_TRY(cudaGetLastError());
-  return FAS_OK;
-}
-
-double stop_value(const fas_ctx* c, double norm) {
-  if (c->p.tol_relative) return norm;
-  return std::pow(c->shape[0].h, c->p.dim / 2.0) * norm;  // Eq. residual: h^{d/2} ||r||_2
+  Prof pr(c, FAS_K_OTHER, 0, (double)n);
+  k_sub_mean<double><<<g, kBlock, 0, c->stream>>>(x, y, n, c->d_scalar + 1);
 }
 
 // One refinement step of the mixed solver: r32 (h32.f[0]) holds b - A u on entry; float32 V-cycles on
@@ -640,77 +617,206 @@ fas_status mixed_step(fas_ctx* c, double* u) {
     Prof pr(c, FAS_K_UPDATE, 0, (double)n);
     k_ir_update<<<grid_for(c, n), kBlock, 0, c->stream>>>(u, H.u[0], n);
   }
+  return FAS_OK;
+}
+
+// The right-hand side the solve works with (the mean-free copy for singular problems).
+const double* solve_rhs(fas_ctx* c, const double* f) { return c->singular ? c->fproj : f; }
+
+// Enqueue everything before the first cycle. fn_ready: S->fn already holds ||f|| (heat steps).
+fas_status enqueue_prologue(fas_ctx* c, double* u, const double* f_in, bool fn_ready, int max_cycles) {
+  const fas_params& p = c->p;
+  SolveState* S = c->S;
+  const double* f = solve_rhs(c, f_in);
+  if (c->singular) {
+    enqueue_remove_mean(c, c->fproj, f_in);
+    fn_ready = false;
+  }
+  if (!fn_ready) enqueue_norm(c, f, nullptr, &S->fn);
+  const double w = p.tol_relative ? 1.0 : std::pow(c->shape[0].h, p.dim / 2.0);  // Eq. residual weight
+  {
+    Prof pr(c, FAS_K_OTHER, 0, 0.0);
+    k_solve_begin<<<1, 1, 0, c->stream>>>(S, p.tol, max_cycles, w, (double)c->shape[0].cells());
+  }
+  enqueue_residual_norm(c, u, f, &S->nscale, &S->res0);
+  Prof pr(c, FAS_K_OTHER, 0, 0.0);
+  k_solve_ref<<<1, 1, 0, c->stream>>>(S, p.tol_relative);
+  return FAS_OK;
+}
+
+// Enqueue one cycle, its residual norm and the stopping decision.
+fas_status enqueue_body(fas_ctx* c, double* u, const double* f_in, cudaGraphConditionalHandle h, int set_cond) {
+  const double* f = solve_rhs(c, f_in);
+  if (c->p.precision == FAS_MIXED) {
+    STATUS_TRY(mixed_step(c, u));
+  } else {
+    STATUS_TRY(vcycle<double>(c, c->h64, u, f));
+  }
+  if (c->singular) enqueue_remove_mean(c, u, u);
+  enqueue_residual_norm(c, u, f, &c->S->nscale, &c->S->res);
+  Prof pr(c, FAS_K_OTHER, 0, 0.0);
+  k_solve_step<<<1, 1, 0, c->stream>>>(c->S, h, set_cond);
+  return FAS_OK;
+}
+
+fas_status read_state(fas_ctx* c) {
+  CUDA_TRY(cudaMemcpyAsync(c->Sh, c->S, sizeof(SolveState), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
   CUDA_TRY(cudaGetLastError());
   return FAS_OK;
 }
 
-// fn_known (nullable): ||f||_2 already computed by the caller (singular problems recompute it)
-fas_status solve_impl(fas_ctx* c, double* u, const double* f_in, fas_info* info, int max_cycles,
-                      const double* fn_known = nullptr) {
-  const fas_params& p = c->p;
-  const int64_t n = c->shape[0].cells();
-  const double* f = f_in;
-  if (c->singular) {
-    STATUS_TRY(remove_mean(c, c->fproj, f_in));
-    f = c->fproj;
-    fn_known = nullptr;
-  }
-  double fn = 0.0;
-  if (fn_known) {
-    fn = *fn_known;
-  } else {
-    STATUS_TRY(norm_of(c, f, 1.f, &fn));
-  }
-  // float squares are exact enough for a stopping test while the rms stays far from the float range
-  // limits; otherwise the norm is recomputed with a power-of-two scale
-  const double rms = fn / std::sqrt((double)n);
-  if (!(rms > 1e-15 && rms < 1e15)) STATUS_TRY(norm_of(c, f, pick_scale(fn, n), &fn));
-  const float ns = pick_scale(fn, n);
-  const bool mixed = p.precision == FAS_MIXED;
-  double rn = 0.0;
-  if (mixed) {
-    STATUS_TRY(p.dim == 2 ? ir_residual<2>(c, u, f, ns, &rn) : ir_residual<3>(c, u, f, ns, &rn));
-  } else {
-    STATUS_TRY(residual_norm64(c, u, f, ns, &rn));
-  }
+fas_status finish_info(fas_ctx* c, fas_info* info, int max_cycles) {
+  const SolveState& S = *c->Sh;
   fas_info loc;
   std::memset(&loc, 0, sizeof(loc));
-  loc.res0 = stop_value(c, rn);
-  const double ref = p.tol_relative ? (fn > 0.0 ? fn : rn) : 1.0;
-  loc.res = loc.res0;
-  loc.rel = ref > 0.0 ? loc.res / ref : 0.0;
-  fas_status st = FAS_ENOTCONV;
-  for (int k = 0; k < max_cycles; ++k) {
-    if (mixed) {
-      STATUS_TRY(mixed_step(c, u));
-    } else {
-      STATUS_TRY(vcycle<double>(c, c->h64, u, f));
-    }
-    if (c->singular) STATUS_TRY(remove_mean(c, u, u));
-    if (mixed) {
-      STATUS_TRY(p.dim == 2 ? ir_residual<2>(c, u, f, ns, &rn) : ir_residual<3>(c, u, f, ns, &rn));
-    } else {
-      STATUS_TRY(residual_norm64(c, u, f, ns, &rn));
-    }
-    loc.cycles++;
-    loc.res = stop_value(c, rn);
-    loc.rel = ref > 0.0 ? loc.res / ref : 0.0;
-    if (!std::isfinite(loc.res)) {
-      st = FAS_ENONFINITE;
-      break;
-    }
-    if (loc.res <= p.tol * ref) {
-      st = FAS_OK;
-      loc.converged = 1;
-      break;
-    }
-  }
+  loc.cycles = S.cycles;
+  loc.converged = S.converged;
+  loc.res0 = S.w * S.res0;
+  loc.res = S.w * S.res;
+  loc.rel = S.ref > 0.0 ? loc.res / S.ref : 0.0;
   loc.rho = (loc.cycles > 0 && loc.res0 > 0.0) ? std::pow(loc.res / loc.res0, 1.0 / loc.cycles) : 0.0;
   if (info) *info = loc;
-  if (st == FAS_ENOTCONV && max_cycles == p.kmax)
-    return fail(st, "fas_solve: tolerance not reached within kmax cycles");
-  if (st == FAS_ENONFINITE) return fail(st, "fas_solve: residual is not finite");
-  return max_cycles == p.kmax ? st : FAS_OK;
+  if (S.nonfinite) return fail(FAS_ENONFINITE, "fas_solve: residual is not finite");
+  if (!S.converged && max_cycles == c->p.kmax)
+    return fail(FAS_ENOTCONV, "fas_solve: tolerance not reached within kmax cycles");
+  return FAS_OK;
+}
+
+// ---- the whole solve as one CUDA graph: prologue, then a while node whose body is one cycle ----
+
+struct CaptureScope {  // switches the launch helpers to counting-only (no event records) while capturing
+  fas_ctx* c;
+  long long start;
+  explicit CaptureScope(fas_ctx* ctx) : c(ctx), start(ctx->launches) { c->capturing = true; }
+  long long count() const { return c->launches - start; }
+  ~CaptureScope() { c->capturing = false; }
+};
+
+void destroy_graphs(fas_ctx* c) {
+  for (auto& g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  c->graphs.clear();
+}
+
+// Build (or find) the graph of a solve of u for f; kind 1 also forms the heat right-hand side
+// b = u + dt fsrc (f = c->b) with its norm at the start.
+fas_status solve_graph(fas_ctx* c, double* u, const double* f, const double* fsrc, double dt, int kind,
+                       SolveGraph** out) {
+  for (auto& g : c->graphs)
+    if (g.u == u && g.f == f && g.fsrc == fsrc && g.dt == dt && g.kind == kind) {
+      *out = &g;
+      return FAS_OK;
+    }
+  SolveGraph g;
+  g.u = u;
+  g.f = f;
+  g.fsrc = fsrc;
+  g.dt = dt;
+  g.kind = kind;
+  CUDA_TRY(cudaGraphCreate(&g.graph, 0));
+  // captured on the context's private streams (the caller's stream may be the legacy default stream,
+  // which cannot be captured); the instantiated graph is launched on the caller's stream
+  cudaStream_t user = c->stream;
+  cudaStream_t main = c->side;
+  fas_status st = FAS_OK;
+  {
+    CaptureScope cap(c);
+    c->stream = main;
+    cudaError_t eb = cudaStreamBeginCaptureToGraph(main, g.graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (eb != cudaSuccess) {
+      c->stream = user;
+      cudaGraphDestroy(g.graph);
+      return fail(FAS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(eb));
+    }
+    const int64_t n = c->shape[0].cells();
+    if (kind == 1) {
+      const int gb = grid_for(c, n);
+      {
+        Prof pr(c, FAS_K_OTHER, 0, (double)n);
+        k_heat_rhs<<<gb, kBlock, 0, main>>>(c->b, u, fsrc, dt, n, c->partials);
+      }
+      Prof pr(c, FAS_K_NORM, 0, 0.0);
+      k_finish_norm<<<1, kBlock, 0, main>>>(c->partials, gb, &c->S->fn, nullptr);
+    }
+    st = enqueue_prologue(c, u, f, kind == 1, c->p.kmax);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNode_t cond_node = nullptr;
+    cudaGraph_t body = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(main, &cs, nullptr, &cg, &deps, nullptr, &nd);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g.graph, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      e = cudaGraphAddNode(&cond_node, cg, deps, nullptr, nd, &np);
+      if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(main, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    cudaError_t e2 = cudaStreamEndCapture(main, &g.graph);
+    if (e != cudaSuccess || e2 != cudaSuccess || st != FAS_OK) {
+      c->stream = user;
+      cudaGraphDestroy(g.graph);
+      return st != FAS_OK ? st : fail(FAS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    g.n_pro = cap.count();
+    // the while node's body: one cycle, its residual norm, the decision
+    const long long before = c->launches;
+    e = cudaStreamBeginCaptureToGraph(c->side2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      c->stream = user;
+      cudaGraphDestroy(g.graph);
+      return fail(FAS_ECUDA, std::string("graph body capture: ") + cudaGetErrorString(e));
+    }
+    c->stream = c->side2;
+    st = enqueue_body(c, u, f, h, 1);
+    c->stream = user;
+    cudaGraph_t body_out = body;
+    e = cudaStreamEndCapture(c->side2, &body_out);
+    if (e != cudaSuccess || st != FAS_OK) {
+      cudaGraphDestroy(g.graph);
+      return st != FAS_OK ? st : fail(FAS_ECUDA, std::string("graph body capture: ") + cudaGetErrorString(e));
+    }
+    g.n_body = c->launches - before;
+  }
+  c->launches -= g.n_pro + g.n_body;  // counted when the graph runs
+  cudaError_t e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g.graph);
+    return fail(FAS_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  c->graphs.push_back(g);
+  *out = &c->graphs.back();
+  return FAS_OK;
+}
+
+// fn_ready: S->fn already holds ||f|| (set by the heat right-hand side kernel)
+fas_status solve_impl(fas_ctx* c, double* u, const double* f, fas_info* info, int max_cycles,
+                      bool fn_ready = false) {
+  const bool graph = c->p.use_graph && !c->prof && max_cycles == c->p.kmax;
+  if (graph) {
+    SolveGraph* g = nullptr;
+    STATUS_TRY(solve_graph(c, u, f, nullptr, 0.0, 0, &g));
+    CUDA_TRY(cudaGraphLaunch(g->exec, c->stream));
+    STATUS_TRY(read_state(c));
+    c->launches += g->n_pro + (long long)c->Sh->cycles * g->n_body;
+    return finish_info(c, info, max_cycles);
+  }
+  STATUS_TRY(enqueue_prologue(c, u, f, fn_ready, max_cycles));
+  for (int k = 0; k < max_cycles; ++k) {
+    STATUS_TRY(enqueue_body(c, u, f, 0, 0));
+    STATUS_TRY(read_state(c));
+    if (!c->Sh->cond) break;
+  }
+  CUDA_TRY(cudaGetLastError());
+  return finish_info(c, info, max_cycles);
 }
 
 fas_status check_ctx(const fas_ctx* c) {
@@ -812,6 +918,11 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
   if (cudaMalloc(&c->partials, c->max_blocks * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "partials"));
   if (cudaMalloc(&c->d_scalar, 8 * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "scalars"));
   if (cudaMallocHost(&c->h_scalar, 8 * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "pinned"));
+  if (cudaMalloc(&c->S, sizeof(SolveState)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "solve state"));
+  if (cudaMallocHost(&c->Sh, sizeof(SolveState)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "pinned state"));
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(FAS_ECUDA, "capture streams"));
   const bool mixed = p.precision == FAS_MIXED;
   st = build_hier<double>(c, c->h64, !mixed, false);
   if (st != FAS_OK) return bail(st);
@@ -821,7 +932,18 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
   }
   if (c->singular && cudaMalloc(&c->fproj, s.cells() * sizeof(double)) != cudaSuccess)
     return bail(fail(FAS_ENOMEM, "fproj"));
-  cudaError_t e = cudaStreamSynchronize(c->stream);
+  // kernel attributes, set before any launch or stream capture
+  cudaError_t e = stream2d_prepare();
+  for (cudaError_t ek : {cudaFuncSetAttribute(k_coarse_smem<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kCoarseSmemLimit),
+                         cudaFuncSetAttribute(k_coarse_smem<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kCoarseSmemLimit),
+                         cudaFuncSetAttribute(k_coarse_smem<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kCoarseSmemLimit),
+                         cudaFuncSetAttribute(k_coarse_smem<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kCoarseSmemLimit)})
+    if (e == cudaSuccess) e = ek;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return bail(fail(FAS_ECUDA, std::string("fas_create: ") + cudaGetErrorString(e)));
   *out = c;
   return FAS_OK;
@@ -837,6 +959,11 @@ fas_status fas_destroy(fas_ctx* c) {
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
   if (c->b) cudaFree(c->b);
   if (c->fproj) cudaFree(c->fproj);
+  destroy_graphs(c);
+  if (c->S) cudaFree(c->S);
+  if (c->Sh) cudaFreeHost(c->Sh);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->side2) cudaStreamDestroy(c->side2);
   if (c->host_u) cudaFree(c->host_u);
   if (c->host_f) cudaFree(c->host_f);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
@@ -866,20 +993,30 @@ fas_status fas_heat_run(fas_ctx* c, double* u, const double* fsrc, double dt, in
   const int64_t n = c->shape[0].cells();
   if (!c->b) CUDA_TRY(cudaMalloc(&c->b, n * sizeof(double)));
   fas_status worst = FAS_OK;
+  const bool graph = c->p.use_graph && !c->prof;
+  SolveGraph* g = nullptr;
+  if (graph) STATUS_TRY(solve_graph(c, u, c->b, fsrc, dt, 1, &g));
   for (int s = 0; s < nsteps; ++s) {
-    const int g = grid_for(c, n);
-    {
-      Prof pr(c, FAS_K_OTHER, 0, (double)n);
-      k_heat_rhs<<<g, kBlock, 0, c->stream>>>(c->b, u, fsrc, dt, n, c->partials);
-    }
-    {
-      Prof pr(c, FAS_K_NORM, 0, 0.0);
-      k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, 1.0);
-    }
-    double bn = 0.0;
-    STATUS_TRY(sync_read(c, &bn));
     fas_info inf;
-    fas_status st = solve_impl(c, u, c->b, &inf, c->p.kmax, &bn);
+    fas_status st;
+    if (graph) {
+      // one graph per time step: b = u + dt fsrc with ||b||, then the solve to tolerance
+      CUDA_TRY(cudaGraphLaunch(g->exec, c->stream));
+      STATUS_TRY(read_state(c));
+      c->launches += g->n_pro + (long long)c->Sh->cycles * g->n_body;
+      st = finish_info(c, &inf, c->p.kmax);
+    } else {
+      const int gb = grid_for(c, n);
+      {
+        Prof pr(c, FAS_K_OTHER, 0, (double)n);
+        k_heat_rhs<<<gb, kBlock, 0, c->stream>>>(c->b, u, fsrc, dt, n, c->partials);
+      }
+      {
+        Prof pr(c, FAS_K_NORM, 0, 0.0);
+        k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, gb, &c->S->fn, nullptr);
+      }
+      st = solve_impl(c, u, c->b, &inf, c->p.kmax, true);
+    }
     if (infos) infos[s] = inf;
     if (st != FAS_OK && st != FAS_ENOTCONV) return st;
     if (st == FAS_ENOTCONV) worst = st;
@@ -907,9 +1044,9 @@ fas_status fas_residual(fas_ctx* c, int level, const double* u, const double* f,
   STATUS_TRY(check_level(c, level, false));
   const LevelDesc<double>& L = c->h64.desc[level];
   if (c->p.dim == 2)
-    launch_residual<double, 2>(c, L, level, out, u, f, 1.f);
+    launch_residual<double, 2>(c, L, level, out, u, f, nullptr, c->d_scalar);
   else
-    launch_residual<double, 3>(c, L, level, out, u, f, 1.f);
+    launch_residual<double, 3>(c, L, level, out, u, f, nullptr, c->d_scalar);
   double v = 0.0;
   STATUS_TRY(sync_read(c, &v));
   if (norm2) *norm2 = v;

@@ -24,6 +24,8 @@
 // Arithmetic per point is the same expression as in basic_kernels.cuh (same association and fma
 // placement), so a V-cycle through these kernels is bit-for-bit the V-cycle of the per-operation
 // float32 kernels.
+#include <mutex>
+
 #include "common.cuh"
 #include "stream2d.h"
 
@@ -484,16 +486,23 @@ cudaError_t launch_stream2d_pre(const float* uin, const float* fin, float* fout,
   return cudaGetLastError();
 }
 
+// Shared-memory size attributes of every fused kernel, set once before any launch or stream capture.
+cudaError_t stream2d_prepare() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    const int big = (int)(sizeof(Ring<true>) * kWarps);
+    cudaError_t e = cudaFuncSetAttribute(k_post<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_post<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    err = e;
+  });
+  return err;
+}
+
 template <int NS, bool UPD>
 cudaError_t post_launch(const float* uin, const float* f, const float* uc, float* uout, double* u64,
                         const LevelDesc<float>& L, int seg, cudaStream_t stream) {
-  constexpr size_t smem = sizeof(Ring<UPD>) * kWarps;
-  static bool attr = false;  // > 48 KB of dynamic shared memory needs the opt-in, once per kernel
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_post<NS, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  constexpr size_t smem = sizeof(Ring<UPD>) * kWarps;  // > 48 KB for UPD: set by stream2d_prepare
   k_post<NS, UPD><<<blocks_for(L.nx, L.ny, seg), kThreads, smem, stream>>>(uin, f, uc, uout, u64, L, seg);
   return cudaGetLastError();
 }

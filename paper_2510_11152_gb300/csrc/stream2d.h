@@ -9,6 +9,9 @@ namespace fasmg {
 constexpr int kStripHalo = 8;                       // recomputed columns on each side of a strip
 constexpr int kStripOut = 32 * 4 - 2 * kStripHalo;  // columns a strip writes (112)
 
+// Set the kernels' shared-memory attributes (once per process; call before launching or capturing).
+cudaError_t stream2d_prepare();
+
 // True if the fused kernels handle a level of nx x ny cells with nu sweeps per smoothing step.
 bool stream2d_supported(int nx, int ny, int nu);
 

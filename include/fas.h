@@ -120,6 +120,32 @@ fas_status fas_heat_run(fas_ctx* ctx, double* u, const double* fsrc, double dt, 
 fas_status fas_heat_run_host(fas_ctx* ctx, const double* u0_host, double* uT_host,
                              const double* fsrc_host, double dt, int nsteps, fas_info* infos);
 
+/* --- many independent problems ----------------------------------------------------------------
+ * Solve count independent problems, problem k on device fields u[k], f[k] with context ctxs[k]
+ * (each context its own size, diffusivity, dt, precision; contexts must be distinct and on the
+ * current device), in ONE launch of one CUDA graph on `stream` (a cudaStream_t, NULL = legacy
+ * default): every problem's solve -- its norms, its initial residual and a device-side while loop
+ * of cycles until its own tolerance or kmax -- is an independent branch of the graph, so small and
+ * large problems run concurrently. The graph is built on the first call for a given list of
+ * (ctx, u, f) and reused afterwards. infos[k] (may be NULL) receives problem k's report. Returns
+ * FAS_ENOTCONV if any problem missed its tolerance, FAS_ENONFINITE if any residual was not finite.
+ * Not in the paper (its problems run one at a time). */
+fas_status fas_solve_batched(fas_ctx* const* ctxs, int count, double* const* u, const double* const* f,
+                             fas_info* infos, void* stream);
+
+/* Autotuning of a context's launch parameters: float32 cycles per refinement step (mixed precision,
+ * 1..3) and the row-segment length of the sweep-fused kernels (auto, 16, 32, 64, 128), chosen by
+ * the time of full solves of f from u = 0 (u is overwritten; a scratch field of the finest size).
+ * Results are cached per (dim, n, precision) for the process, so contexts of a size already tuned
+ * take the cached choice without timing. out (may be NULL) receives the choice and its time. */
+typedef struct {
+  int inner_cycles, seg_rows;
+  double ms;           /* time of one solve with the chosen parameters                           */
+  int candidates;      /* number of parameter sets timed (0 when the cached choice was used)      */
+} fas_tune_result;
+
+fas_status fas_autotune(fas_ctx* ctx, double* u_scratch, const double* f, fas_tune_result* out);
+
 /* --- single operators, for testing each kernel against the oracle ---------------------------- */
 
 /* out = f - A u on level `level` (Sec. 2.2, r = f - L_h p), norm2 (may be NULL) = ||out||_2.

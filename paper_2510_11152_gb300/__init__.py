@@ -22,7 +22,8 @@ __all__ = [
     "FasError", "fas_params", "fas_info", "load", "fas_default_params", "fas_create", "fas_destroy",
     "fas_num_levels", "fas_vcycle", "fas_solve", "fas_heat_run", "fas_heat_run_host", "fas_residual",
     "fas_smooth", "fas_restrict", "fas_prolong_add", "fas_last_error", "fas_launch_count", "Solver",
-    "fas_prof_enable", "fas_prof_read", "make_params", "fas_vcycle_small_static",
+    "fas_prof_enable", "fas_prof_read", "make_params", "fas_vcycle_small_static", "fas_solve_batched",
+    "fas_autotune",
 ]
 
 FAS_OK, FAS_EINVAL, FAS_ENOMEM, FAS_ENOTCONV, FAS_ENONFINITE, FAS_ETIMEOUT, FAS_ECUDA, FAS_EUNSUPPORTED = range(8)
@@ -47,6 +48,14 @@ class fas_params(ctypes.Structure):
 class fas_info(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("converged", ctypes.c_int), ("res0", ctypes.c_double),
                 ("res", ctypes.c_double), ("rel", ctypes.c_double), ("rho", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fas_tune_result(ctypes.Structure):
+    _fields_ = [("inner_cycles", ctypes.c_int), ("seg_rows", ctypes.c_int), ("ms", ctypes.c_double),
+                ("candidates", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,6 +100,9 @@ def load(path: str | None = None):
         "fas_launch_count": (ctypes.c_longlong, [_P, _I]),
         "fas_prof_enable": (_I, [_P, _I]),
         "fas_vcycle_small_static": (_I, [ctypes.POINTER(fas_params), _P, _P, _I, ctypes.POINTER(_D), _P]),
+        "fas_solve_batched": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                   ctypes.POINTER(fas_info), _P]),
+        "fas_autotune": (_I, [_P, _P, _P, ctypes.POINTER(fas_tune_result)]),
         "fas_prof_read": (_I, [_P, ctypes.c_void_p, _I, ctypes.POINTER(_I)]),
     }
     for name, (res, args) in sig.items():
@@ -255,6 +267,31 @@ def fas_vcycle_small_static(params: fas_params, u, f, ncycles: int, stream=None,
                                         ctypes.byref(res) if want_res else None, _stream_handle(stream))
     _check(st, "fas_vcycle_small_static")
     return res.value if want_res else None
+
+
+def fas_solve_batched(ctxs, us, fs, stream=None, allow_notconv=False):
+    """Solve independent problems (one context each) in one graph launch; returns their fas_info."""
+    n = len(ctxs)
+    if not (len(us) == len(fs) == n) or n == 0:
+        raise ValueError("need equal, non-empty lists of contexts, u and f")
+    harr = (_P * n)(*[c.handle for c in ctxs])
+    uarr = (_P * n)(*[_dev(u, "u", c.cells) for c, u in zip(ctxs, us)])
+    farr = (_P * n)(*[_dev(f, "f", c.cells) for c, f in zip(ctxs, fs)])
+    infos = (fas_info * n)()
+    st = load().fas_solve_batched(harr, n, uarr, farr, infos, _stream_handle(stream))
+    if not (allow_notconv and st == FAS_ENOTCONV):
+        _check(st, "fas_solve_batched")
+    return [infos[k] for k in range(n)]
+
+
+def fas_autotune(ctx: _Ctx, u_scratch, f) -> dict:
+    """Choose the context's launch parameters by timing whole solves (cached per size class)."""
+    out = fas_tune_result()
+    _check(load().fas_autotune(ctx.handle, _dev(u_scratch, "u_scratch", ctx.cells), _dev(f, "f", ctx.cells),
+                               ctypes.byref(out)), "fas_autotune")
+    ctx.params.inner_cycles = out.inner_cycles
+    ctx.params.seg_rows = out.seg_rows
+    return out.as_dict()
 
 
 def fas_launch_count(ctx: _Ctx, reset: bool = False) -> int:

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -819,6 +820,151 @@ fas_status solve_impl(fas_ctx* c, double* u, const double* f, fas_info* info, in
   return finish_info(c, info, max_cycles);
 }
 
+// ---------------------------------------------------------------------------------------------
+// batched solves: one graph, one branch per problem
+// ---------------------------------------------------------------------------------------------
+
+__global__ void k_copy_state(SolveState* dst, const SolveState* src) { *dst = *src; }
+
+struct BatchGraph {
+  std::vector<fas_ctx*> ctxs;
+  std::vector<double*> u;
+  std::vector<const double*> f;
+  std::vector<long long> n_pro, n_body;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  SolveState* d_states = nullptr;
+  SolveState* h_states = nullptr;
+};
+
+std::mutex g_batch_mutex;
+std::vector<BatchGraph*> g_batches;  // built batch graphs, dropped when one of their contexts is destroyed
+
+void free_batch(BatchGraph* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->d_states) cudaFree(b->d_states);
+  if (b->h_states) cudaFreeHost(b->h_states);
+  delete b;
+}
+
+void drop_batches_of(const fas_ctx* c) {
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  for (size_t k = 0; k < g_batches.size();) {
+    BatchGraph* b = g_batches[k];
+    if (std::find(b->ctxs.begin(), b->ctxs.end(), c) != b->ctxs.end()) {
+      free_batch(b);
+      g_batches.erase(g_batches.begin() + k);
+    } else {
+      ++k;
+    }
+  }
+}
+
+fas_status build_batch(BatchGraph* B) {
+  const int n = (int)B->ctxs.size();
+  CUDA_TRY(cudaMalloc(&B->d_states, n * sizeof(SolveState)));
+  CUDA_TRY(cudaMallocHost(&B->h_states, n * sizeof(SolveState)));
+  CUDA_TRY(cudaGraphCreate(&B->graph, 0));
+  cudaStream_t org = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins(n, nullptr);
+  std::vector<cudaGraph_t> bodies(n, nullptr);
+  std::vector<cudaGraphConditionalHandle> handles(n, 0);
+  B->n_pro.assign(n, 0);
+  B->n_body.assign(n, 0);
+  fas_status st = FAS_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&org, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(org, B->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaEventRecord(fork, org);
+  // prologue and while node of every problem, each on its own context's capture stream
+  for (int i = 0; i < n && e == cudaSuccess && st == FAS_OK; ++i) {
+    fas_ctx* c = B->ctxs[i];
+    cudaStream_t sv = c->stream;
+    cudaStream_t cs = c->side;
+    e = cudaStreamWaitEvent(cs, fork, 0);
+    if (e != cudaSuccess) break;
+    c->stream = cs;
+    {
+      CaptureScope cap(c);
+      st = enqueue_prologue(c, B->u[i], B->f[i], false, c->p.kmax);
+      B->n_pro[i] = cap.count() + 1;  // + the state copy below
+    }
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphNode_t cond_node = nullptr;
+    if (st == FAS_OK) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd);
+    if (st == FAS_OK && e == cudaSuccess)
+      e = cudaGraphConditionalHandleCreate(&handles[i], B->graph, 1, cudaGraphCondAssignDefault);
+    if (st == FAS_OK && e == cudaSuccess) {
+      cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+      np.conditional.handle = handles[i];
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      e = cudaGraphAddNode(&cond_node, cg, deps, nullptr, nd, &np);
+      if (e == cudaSuccess) bodies[i] = np.conditional.phGraph_out[0];
+    }
+    if (st == FAS_OK && e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(cs, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (st == FAS_OK && e == cudaSuccess) {
+      k_copy_state<<<1, 1, 0, cs>>>(B->d_states + i, c->S);
+      e = cudaEventRecord(joins[i], cs);
+    }
+    if (st == FAS_OK && e == cudaSuccess) e = cudaStreamWaitEvent(org, joins[i], 0);
+    c->stream = sv;
+  }
+  cudaGraph_t g_out = B->graph;
+  cudaError_t e2 = cudaStreamEndCapture(org, &g_out);
+  if (e == cudaSuccess) e = e2;
+  // bodies: one cycle, its residual norm and the decision, per problem
+  for (int i = 0; i < n && e == cudaSuccess && st == FAS_OK; ++i) {
+    fas_ctx* c = B->ctxs[i];
+    cudaStream_t sv = c->stream;
+    e = cudaStreamBeginCaptureToGraph(c->side2, bodies[i], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    c->stream = c->side2;
+    {
+      CaptureScope cap(c);
+      st = enqueue_body(c, B->u[i], B->f[i], handles[i], 1);
+      B->n_body[i] = cap.count();
+    }
+    c->stream = sv;
+    cudaGraph_t b_out = bodies[i];
+    e2 = cudaStreamEndCapture(c->side2, &b_out);
+    if (e == cudaSuccess) e = e2;
+  }
+  for (int i = 0; i < n; ++i) B->ctxs[i]->launches -= B->n_pro[i] - 1 + B->n_body[i];  // counted at run time
+  if (e == cudaSuccess && st == FAS_OK) e = cudaGraphInstantiate(&B->exec, B->graph, 0);
+  for (auto ev : joins)
+    if (ev) cudaEventDestroy(ev);
+  if (fork) cudaEventDestroy(fork);
+  if (org) cudaStreamDestroy(org);
+  if (st != FAS_OK) return st;
+  if (e != cudaSuccess) return fail(FAS_ECUDA, std::string("batched graph: ") + cudaGetErrorString(e));
+  return FAS_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// autotuning: launch parameters chosen by timing whole solves, cached per size class
+// ---------------------------------------------------------------------------------------------
+
+struct TuneKey {
+  int dim, nx, ny, nz, precision;
+  bool operator==(const TuneKey& o) const {
+    return dim == o.dim && nx == o.nx && ny == o.ny && nz == o.nz && precision == o.precision;
+  }
+};
+struct TuneEntry {
+  TuneKey key;
+  fas_tune_result res;
+};
+std::mutex g_tune_mutex;
+std::vector<TuneEntry> g_tune_cache;
+
 fas_status check_ctx(const fas_ctx* c) {
   if (!c) return fail(FAS_EINVAL, "null context");
   return FAS_OK;
@@ -951,6 +1097,7 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
 
 fas_status fas_destroy(fas_ctx* c) {
   if (!c) return FAS_OK;
+  drop_batches_of(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_hier(c->h64);
   free_hier(c->h32);
@@ -1038,6 +1185,130 @@ fas_status fas_heat_run_host(fas_ctx* c, const double* u0_host, double* uT_host,
   CUDA_TRY(cudaMemcpyAsync(uT_host, c->host_u, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return st;
+}
+
+fas_status fas_solve_batched(fas_ctx* const* ctxs, int count, double* const* u, const double* const* f,
+                             fas_info* infos, void* stream) {
+  if (!ctxs || !u || !f || count < 1) return fail(FAS_EINVAL, "fas_solve_batched: bad arguments");
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i] || !u[i] || !f[i]) return fail(FAS_EINVAL, "fas_solve_batched: null context or field");
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return fail(FAS_EINVAL, "fas_solve_batched: a context appears twice");
+    if (ctxs[i]->prof) return fail(FAS_EINVAL, "fas_solve_batched: kernel timing is on for a context");
+  }
+  BatchGraph* B = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    for (BatchGraph* b : g_batches) {
+      if ((int)b->ctxs.size() != count) continue;
+      bool same = true;
+      for (int i = 0; i < count && same; ++i) same = b->ctxs[i] == ctxs[i] && b->u[i] == u[i] && b->f[i] == f[i];
+      if (same) {
+        B = b;
+        break;
+      }
+    }
+  }
+  if (!B) {
+    B = new BatchGraph();
+    B->ctxs.assign(ctxs, ctxs + count);
+    B->u.assign(u, u + count);
+    B->f.assign(f, f + count);
+    fas_status st = build_batch(B);
+    if (st != FAS_OK) {
+      free_batch(B);
+      return st;
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    g_batches.push_back(B);
+  }
+  cudaStream_t st_ = (cudaStream_t)stream;
+  CUDA_TRY(cudaGraphLaunch(B->exec, st_));
+  CUDA_TRY(cudaMemcpyAsync(B->h_states, B->d_states, count * sizeof(SolveState), cudaMemcpyDeviceToHost, st_));
+  CUDA_TRY(cudaStreamSynchronize(st_));
+  CUDA_TRY(cudaGetLastError());
+  fas_status worst = FAS_OK;
+  for (int i = 0; i < count; ++i) {
+    fas_ctx* c = ctxs[i];
+    *c->Sh = B->h_states[i];
+    c->launches += B->n_pro[i] + (long long)B->h_states[i].cycles * B->n_body[i];
+    fas_info inf;
+    const fas_status st = finish_info(c, &inf, c->p.kmax);
+    if (infos) infos[i] = inf;
+    if (st == FAS_ENONFINITE || (st != FAS_OK && worst == FAS_OK)) worst = st;
+  }
+  if (worst == FAS_ENOTCONV) return fail(worst, "fas_solve_batched: a problem missed its tolerance within kmax");
+  if (worst == FAS_ENONFINITE) return fail(worst, "fas_solve_batched: a residual is not finite");
+  return worst;
+}
+
+fas_status fas_autotune(fas_ctx* c, double* u, const double* f, fas_tune_result* out) {
+  STATUS_TRY(check_ctx(c));
+  if (!u || !f) return fail(FAS_EINVAL, "fas_autotune: null field");
+  const TuneKey key{c->p.dim, c->shape[0].nx, c->shape[0].ny, c->shape[0].nz, c->p.precision};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (const TuneEntry& t : g_tune_cache)
+      if (t.key == key) {
+        c->p.inner_cycles = t.res.inner_cycles;
+        c->p.seg_rows = t.res.seg_rows;
+        destroy_graphs(c);
+        drop_batches_of(c);
+        if (out) {
+          *out = t.res;
+          out->candidates = 0;
+        }
+        return FAS_OK;
+      }
+  }
+  const bool mixed = c->p.precision == FAS_MIXED;
+  const bool fused = mixed && c->h32.nfast > 0;
+  const int inners[3] = {1, 2, 3};
+  const int segs[5] = {0, 16, 32, 64, 128};
+  const int n_inner = mixed ? 3 : 1, n_seg = fused ? 5 : 1;
+  const int64_t n = c->shape[0].cells();
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  fas_tune_result best{c->p.inner_cycles, c->p.seg_rows, 1e300, 0};
+  const int keep_inner = c->p.inner_cycles, keep_seg = c->p.seg_rows;
+  fas_status st = FAS_OK;
+  for (int a = 0; a < n_inner && st == FAS_OK; ++a)
+    for (int b = 0; b < n_seg && st == FAS_OK; ++b) {
+      c->p.inner_cycles = mixed ? inners[a] : keep_inner;
+      c->p.seg_rows = fused ? segs[b] : keep_seg;
+      destroy_graphs(c);
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && st == FAS_OK; ++rep) {  // the first run captures the graph
+        cudaMemsetAsync(u, 0, n * sizeof(double), c->stream);
+        cudaEventRecord(e0, c->stream);
+        fas_info inf;
+        st = solve_impl(c, u, f, &inf, c->p.kmax);
+        if (st == FAS_ENOTCONV) st = FAS_OK;  // a slow candidate still has a time
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      best.candidates++;
+      if (st == FAS_OK && ms < best.ms) {
+        best.ms = ms;
+        best.inner_cycles = c->p.inner_cycles;
+        best.seg_rows = c->p.seg_rows;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->p.inner_cycles = best.inner_cycles;
+  c->p.seg_rows = best.seg_rows;
+  destroy_graphs(c);
+  drop_batches_of(c);
+  if (st != FAS_OK) return st;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache.push_back(TuneEntry{key, best});
+  }
+  if (out) *out = best;
+  return FAS_OK;
 }
 
 fas_status fas_residual(fas_ctx* c, int level, const double* u, const double* f, double* out, double* norm2) {

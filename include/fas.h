@@ -114,6 +114,20 @@ fas_status fas_solve(fas_ctx* ctx, double* u, const double* f, fas_info* info);
 fas_status fas_heat_run(fas_ctx* ctx, double* u, const double* fsrc, double dt, int nsteps,
                         fas_info* infos);
 
+/* Adjoint of fas_heat_run (not in the paper): given dL/du^N for a loss L of the final state of
+ * nsteps backward-Euler steps from u0 (device fields), computes the gradients of L with respect to
+ * u0, the source fsrc and the per-cell diffusivity of the context (the field passed as kappa to
+ * fas_create; with a constant kappa g_kappa is the gradient with respect to a per-cell field at that
+ * value). A = I - dt div(kappa grad) is symmetric, so each backward step is a solve with the same
+ * multigrid:  mu = A^{-1} lambda,  g_f += dt mu,  g_kappa += -(d(mu^T A u^{n+1})/d kappa),
+ * lambda <- mu, starting from lambda = dL/du^N; g_u0 = lambda at the end. Forward states are kept
+ * every ckpt_every steps (<= 0: every step) and recomputed segment by segment in the backward sweep.
+ * uT (may be NULL) receives u^N; g_u0, g_f, g_kappa may each be NULL. fsrc may be NULL (no source).
+ * The context must have alpha = 1 and beta = dt. All pointers are DEVICE pointers. */
+fas_status fas_heat_adjoint(fas_ctx* ctx, const double* u0, const double* fsrc, double dt, int nsteps,
+                            const double* dL_duT, double* uT, double* g_u0, double* g_f, double* g_kappa,
+                            int ckpt_every);
+
 /* fas_heat_run with HOST buffers (pinned memory gives the fastest copies): copies u0_host and
  * fsrc_host (may be NULL) to device buffers the context keeps between calls, runs nsteps steps and
  * copies the result to uT_host (may equal u0_host). Returns after the result is on the host. */

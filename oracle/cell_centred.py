@@ -472,3 +472,62 @@ def heat_run(op: Operator, u0: np.ndarray, fsrc, dt: float, nsteps: int, params:
         else:
             infos.append(solve(levels, u, b, params))
     return u, infos
+
+
+# ---------------------------------------------------------------------------------------------
+# adjoint of backward-Euler heat stepping (not in the paper)
+# ---------------------------------------------------------------------------------------------
+
+def kappa_gradient(op: Operator, u: np.ndarray, mu: np.ndarray) -> np.ndarray:
+    """-(d(mu^T A u) / d kappa) per cell for A u = alpha u - beta div(kappa grad u) with face kappa
+    the mean of its two cells (reading G8): an interior face between cells c and nb contributes
+    -(beta/h^2) (u_nb - u_c)(mu_nb - mu_c), half to each cell; a Dirichlet face (ghost -u_c, face
+    kappa = kappa_c) contributes -(2 beta/h^2) mu_c u_c to its cell; Neumann faces carry no flux."""
+    g = np.zeros(op.shape)
+    scale = op.beta / (op.h * op.h)
+    for ax in range(op.dim):
+        n = op.shape[ax]
+        du = np.diff(u, axis=ax)
+        dmu = np.diff(mu, axis=ax)
+        face = -scale * du * dmu  # dL/d kappa_f of each interior face
+        lo = [slice(None)] * op.dim
+        lo[ax] = slice(0, n - 1)
+        hi = [slice(None)] * op.dim
+        hi[ax] = slice(1, n)
+        g[tuple(lo)] += 0.5 * face
+        g[tuple(hi)] += 0.5 * face
+        lo_kind, hi_kind = op.axis_bc(ax)
+        for kind, idx in ((lo_kind, 0), (hi_kind, n - 1)):
+            if kind == DIRICHLET:
+                sl = [slice(None)] * op.dim
+                sl[ax] = idx
+                g[tuple(sl)] -= 2.0 * scale * mu[tuple(sl)] * u[tuple(sl)]
+    return g
+
+
+def adjoint_heat(op: Operator, u0: np.ndarray, fsrc, dt: float, nsteps: int, dL_duT: np.ndarray,
+                 params: Params):
+    """Gradients of a loss L(u^N) of the backward-Euler run (A u^{n+1} = u^n + dt f, A symmetric)
+    with respect to u^0, f and kappa, given dL/du^N:
+        lambda^N = dL/du^N;  for n = N-1..0:  mu = A^{-1} lambda^{n+1},
+        dL/df += dt mu,  dL/dkappa += kappa_gradient(u^{n+1}, mu),  lambda^n = mu;
+        dL/du^0 = lambda^0.
+    Every state of the forward run is kept (no checkpointing: small problems only)."""
+    levels = build_levels(op, params.coarsest)
+    f = np.zeros(op.shape) if fsrc is None else np.asarray(fsrc, dtype=np.float64)
+    states = [np.array(u0, dtype=np.float64, copy=True)]
+    u = states[0].copy()
+    for _ in range(nsteps):
+        b = u + dt * f
+        solve(levels, u, b, params)
+        states.append(u.copy())
+    lam = np.array(dL_duT, dtype=np.float64, copy=True)
+    g_f = np.zeros(op.shape)
+    g_k = np.zeros(op.shape)
+    for n in range(nsteps - 1, -1, -1):
+        mu = lam.copy()  # initial guess
+        solve(levels, mu, lam, params)
+        g_f += dt * mu
+        g_k += kappa_gradient(op, states[n + 1], mu)
+        lam = mu
+    return states[-1], lam, g_f, g_k

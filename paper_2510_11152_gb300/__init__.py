@@ -23,7 +23,7 @@ __all__ = [
     "fas_num_levels", "fas_vcycle", "fas_solve", "fas_heat_run", "fas_heat_run_host", "fas_residual",
     "fas_smooth", "fas_restrict", "fas_prolong_add", "fas_last_error", "fas_launch_count", "Solver",
     "fas_prof_enable", "fas_prof_read", "make_params", "fas_vcycle_small_static", "fas_solve_batched",
-    "fas_autotune",
+    "fas_autotune", "fas_heat_adjoint",
 ]
 
 FAS_OK, FAS_EINVAL, FAS_ENOMEM, FAS_ENOTCONV, FAS_ENONFINITE, FAS_ETIMEOUT, FAS_ECUDA, FAS_EUNSUPPORTED = range(8)
@@ -103,6 +103,7 @@ def load(path: str | None = None):
         "fas_solve_batched": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                    ctypes.POINTER(fas_info), _P]),
         "fas_autotune": (_I, [_P, _P, _P, ctypes.POINTER(fas_tune_result)]),
+        "fas_heat_adjoint": (_I, [_P, _P, _P, _D, _I, _P, _P, _P, _P, _P, _I]),
         "fas_prof_read": (_I, [_P, ctypes.c_void_p, _I, ctypes.POINTER(_I)]),
     }
     for name, (res, args) in sig.items():
@@ -282,6 +283,16 @@ def fas_solve_batched(ctxs, us, fs, stream=None, allow_notconv=False):
     if not (allow_notconv and st == FAS_ENOTCONV):
         _check(st, "fas_solve_batched")
     return [infos[k] for k in range(n)]
+
+
+def fas_heat_adjoint(ctx: _Ctx, u0, fsrc, dt: float, nsteps: int, dL_duT, uT=None, g_u0=None, g_f=None,
+                     g_kappa=None, ckpt_every: int = 10) -> None:
+    """Gradients of a loss of the final heat state (see include/fas.h); outputs written in place."""
+    n = ctx.cells
+    _check(load().fas_heat_adjoint(ctx.handle, _dev(u0, "u0", n), _dev(fsrc, "fsrc", n), float(dt), int(nsteps),
+                                   _dev(dL_duT, "dL_duT", n), _dev(uT, "uT", n), _dev(g_u0, "g_u0", n),
+                                   _dev(g_f, "g_f", n), _dev(g_kappa, "g_kappa", n), int(ckpt_every)),
+           "fas_heat_adjoint")
 
 
 def fas_autotune(ctx: _Ctx, u_scratch, f) -> dict:

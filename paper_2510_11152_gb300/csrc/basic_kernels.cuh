@@ -433,6 +433,51 @@ __global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayou
 }
 
 // ------------------------------------------------------------------------------------------------
+// Adjoint of backward-Euler heat stepping: -(d(mu^T A u)/d kappa) per cell, added to g. Interior face
+// c|nb: -(beta/h^2)(u_nb - u_c)(mu_nb - mu_c), half to each cell (face kappa = mean of the two
+// cells); Dirichlet face: -(2 beta/h^2) mu_c u_c (face kappa = cell kappa); Neumann faces: nothing.
+// scale = beta / h^2; dir[f] = 1 for a Dirichlet face f (x_lo, x_hi, y_lo, y_hi, z_lo, z_hi).
+// ------------------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void k_kappa_grad(double* g, const double* u, const double* mu, int nx, int ny, int nz, int lx, int ly,
+                             double scale, int dirmask) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  for (int64_t idx = gtid(); idx < n; idx += gstride()) {
+    const int i = (int)(idx & (nx - 1));
+    const int j = (int)((idx >> lx) & (ny - 1));
+    const int l = (int)(idx >> (lx + ly));
+    const double uc = u[idx], mc = mu[idx];
+    double acc = 0.0;
+    if (i > 0) acc += (u[idx - 1] - uc) * (mu[idx - 1] - mc);
+    if (i < nx - 1) acc += (u[idx + 1] - uc) * (mu[idx + 1] - mc);
+    if (j > 0) acc += (u[idx - sy] - uc) * (mu[idx - sy] - mc);
+    if (j < ny - 1) acc += (u[idx + sy] - uc) * (mu[idx + sy] - mc);
+    if (DIM == 3) {
+      if (l > 0) acc += (u[idx - sz] - uc) * (mu[idx - sz] - mc);
+      if (l < nz - 1) acc += (u[idx + sz] - uc) * (mu[idx + sz] - mc);
+    }
+    double v = -0.5 * scale * acc;
+    int nd = 0;  // Dirichlet faces of this cell
+    nd += (i == 0) & (dirmask & 1);
+    nd += (i == nx - 1) & ((dirmask >> 1) & 1);
+    nd += (j == 0) & ((dirmask >> 2) & 1);
+    nd += (j == ny - 1) & ((dirmask >> 3) & 1);
+    if (DIM == 3) {
+      nd += (l == 0) & ((dirmask >> 4) & 1);
+      nd += (l == nz - 1) & ((dirmask >> 5) & 1);
+    }
+    if (nd) v -= 2.0 * scale * nd * mc * uc;
+    g[idx] += v;
+  }
+}
+
+// y += a x
+static __global__ void k_axpy(double* y, double a, const double* x, int64_t n) {
+  for (int64_t i = gtid(); i < n; i += gstride()) y[i] = fma(a, x[i], y[i]);
+}
+
+// ------------------------------------------------------------------------------------------------
 // Device-side state of one solve (Algorithm 1's outer loop): the stopping decision is taken on the
 // device, so that the same kernels serve a host-driven loop and a graph with a conditional node.
 // ------------------------------------------------------------------------------------------------

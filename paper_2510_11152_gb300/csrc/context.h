@@ -78,6 +78,7 @@ struct fas_ctx {
   double* h_scalar = nullptr;  // pinned host mirror
   double* b = nullptr;         // heat-step right-hand side (fine, float64)
   double* fproj = nullptr;     // mean-free copy of f for singular problems
+  std::vector<double*> adj;     // adjoint buffers: checkpoints, segment states, lambda, mu, work
   double* host_u = nullptr;    // device buffers of fas_heat_run_host
   double* host_f = nullptr;
   long long launches = 0;

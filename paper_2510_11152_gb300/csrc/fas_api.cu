@@ -1111,6 +1111,7 @@ fas_status fas_destroy(fas_ctx* c) {
   if (c->Sh) cudaFreeHost(c->Sh);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->side2) cudaStreamDestroy(c->side2);
+  for (double* q : c->adj) cudaFree(q);
   if (c->host_u) cudaFree(c->host_u);
   if (c->host_f) cudaFree(c->host_f);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
@@ -1169,6 +1170,95 @@ fas_status fas_heat_run(fas_ctx* c, double* u, const double* fsrc, double dt, in
     if (st == FAS_ENOTCONV) worst = st;
   }
   return worst;
+}
+
+fas_status fas_heat_adjoint(fas_ctx* c, const double* u0, const double* fsrc, double dt, int nsteps,
+                            const double* dL_duT, double* uT, double* g_u0, double* g_f, double* g_kappa,
+                            int ckpt_every) {
+  STATUS_TRY(check_ctx(c));
+  if (!u0 || !dL_duT || nsteps < 1) return fail(FAS_EINVAL, "fas_heat_adjoint: bad argument");
+  if (c->p.alpha != 1.0 || std::fabs(c->p.beta - dt) > 1e-15 * std::fabs(dt))
+    return fail(FAS_EINVAL, "fas_heat_adjoint: context must have alpha = 1 and beta = dt");
+  const int64_t n = c->shape[0].cells();
+  const size_t bytes = n * sizeof(double);
+  const int K = ckpt_every > 0 ? std::min(ckpt_every, nsteps) : nsteps;
+  const int nseg = (nsteps + K - 1) / K;
+  // buffers: nseg checkpoints, K + 1 segment states, lambda, mu, work
+  const size_t need = (size_t)nseg + K + 1 + 3;
+  while (c->adj.size() < need) {
+    double* q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) return fail(FAS_ENOMEM, "fas_heat_adjoint: buffers");
+    c->adj.push_back(q);
+  }
+  double** ckpt = c->adj.data();
+  double** seg = c->adj.data() + nseg;
+  double* lam = c->adj[nseg + K + 1];
+  double* mu = c->adj[nseg + K + 2];
+  double* work = c->adj[nseg + K + 3];
+  cudaStream_t st = c->stream;
+  fas_status worst = FAS_OK;
+  auto step = [&](double* u) -> fas_status {  // one backward-Euler step in place
+    fas_info inf;
+    fas_status s2 = fas_heat_run(c, u, fsrc, dt, 1, &inf);
+    if (s2 == FAS_ENOTCONV) {
+      worst = s2;
+      return FAS_OK;
+    }
+    return s2;
+  };
+  // forward sweep, keeping every K-th state
+  CUDA_TRY(cudaMemcpyAsync(work, u0, bytes, cudaMemcpyDeviceToDevice, st));
+  for (int k = 0; k < nsteps; ++k) {
+    if (k % K == 0) CUDA_TRY(cudaMemcpyAsync(ckpt[k / K], work, bytes, cudaMemcpyDeviceToDevice, st));
+    STATUS_TRY(step(work));
+  }
+  if (uT) CUDA_TRY(cudaMemcpyAsync(uT, work, bytes, cudaMemcpyDeviceToDevice, st));
+  // backward sweep
+  CUDA_TRY(cudaMemcpyAsync(lam, dL_duT, bytes, cudaMemcpyDeviceToDevice, st));
+  if (g_f) CUDA_TRY(cudaMemsetAsync(g_f, 0, bytes, st));
+  if (g_kappa) CUDA_TRY(cudaMemsetAsync(g_kappa, 0, bytes, st));
+  const LevelShape& s0 = c->shape[0];
+  int dirmask = 0;
+  for (int fc = 0; fc < 2 * c->p.dim; ++fc) dirmask |= (c->p.bc[fc] == FAS_BC_DIRICHLET) << fc;
+  const double scale = c->p.beta / (s0.h * s0.h);
+  const int lx = c->h64.desc[0].lx, ly = c->h64.desc[0].ly;
+  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+    const int n0 = sgi * K, n1 = std::min(n0 + K, nsteps);
+    // recompute the segment's states u^{n0}..u^{n1}
+    CUDA_TRY(cudaMemcpyAsync(work, ckpt[sgi], bytes, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(seg[0], work, bytes, cudaMemcpyDeviceToDevice, st));
+    for (int j = 1; j <= n1 - n0; ++j) {
+      STATUS_TRY(step(work));
+      CUDA_TRY(cudaMemcpyAsync(seg[j], work, bytes, cudaMemcpyDeviceToDevice, st));
+    }
+    for (int k = n1 - 1; k >= n0; --k) {
+      // mu = A^{-1} lambda (A symmetric), started from lambda
+      CUDA_TRY(cudaMemcpyAsync(mu, lam, bytes, cudaMemcpyDeviceToDevice, st));
+      fas_info inf;
+      fas_status s2 = solve_impl(c, mu, lam, &inf, c->p.kmax);
+      if (s2 == FAS_ENOTCONV) worst = s2;
+      else if (s2 != FAS_OK) return s2;
+      if (g_f) {
+        Prof pr(c, FAS_K_OTHER, 0, (double)n);
+        k_axpy<<<grid_for(c, n), kBlock, 0, st>>>(g_f, dt, mu, n);
+      }
+      if (g_kappa) {
+        Prof pr(c, FAS_K_OTHER, 0, (double)n);
+        if (c->p.dim == 2)
+          k_kappa_grad<2><<<grid_for(c, n), kBlock, 0, st>>>(g_kappa, seg[k + 1 - n0], mu, s0.nx, s0.ny, s0.nz, lx,
+                                                             ly, scale, dirmask);
+        else
+          k_kappa_grad<3><<<grid_for(c, n), kBlock, 0, st>>>(g_kappa, seg[k + 1 - n0], mu, s0.nx, s0.ny, s0.nz, lx,
+                                                             ly, scale, dirmask);
+      }
+      std::swap(lam, mu);
+    }
+  }
+  if (g_u0) CUDA_TRY(cudaMemcpyAsync(g_u0, lam, bytes, cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  CUDA_TRY(cudaGetLastError());
+  if (worst != FAS_OK) return fail(worst, "fas_heat_adjoint: a solve missed its tolerance within kmax");
+  return FAS_OK;
 }
 
 fas_status fas_heat_run_host(fas_ctx* c, const double* u0_host, double* uT_host, const double* fsrc_host, double dt,

@@ -1,0 +1,164 @@
+"""Pins of the staggered-grid oracle (face operator, face X-MCGS, Appendix D transfers, projection)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cell_centred as cc
+from oracle import staggered as st
+from workloads import random_field
+
+
+def _face_mode(shape, comp, ks, h):
+    """sin(k pi x) at the normal faces (x = (s+1) h, 0 at the wall slot) times cell-centred Dirichlet
+    sine modes sin(k pi (j + 1/2) h) along the tangential axes; eigenvalue of -Lap: sum of
+    (4/h^2) sin^2(k pi h / 2)."""
+    dim = len(shape)
+    fax = dim - 1 - comp
+    v = np.ones(shape)
+    lam = 0.0
+    for ax in range(dim):
+        n = shape[ax]
+        k = ks[ax]
+        L = n * h  # length of this axis
+        if ax == fax:
+            x = (np.arange(n) + 1.0) * h
+            m = np.sin(k * math.pi * x / L)
+            m[-1] = 0.0
+        else:
+            x = (np.arange(n) + 0.5) * h
+            m = np.sin(k * math.pi * x / L)
+        lam += 4.0 / h ** 2 * math.sin(k * math.pi * h / (2 * L)) ** 2
+        sh = [1] * dim
+        sh[ax] = n
+        v = v * m.reshape(sh)
+    return v, lam
+
+
+@pytest.mark.parametrize("shape,comp", [((8, 16), 0), ((8, 16), 1), ((8, 8, 8), 0), ((4, 8, 8), 2)])
+def test_face_operator_eigenpairs(shape, comp):
+    h = 1.0 / shape[-1]
+    op = st.FaceOperator(shape, h, 0.7, 0.01, comp)
+    dim = len(shape)
+    for ks in [(1,) * dim, (2, 3, 1)[:dim], (3, 1, 2)[:dim]]:
+        v, lam = _face_mode(shape, comp, ks, h)
+        np.testing.assert_allclose(st.apply_A_face(op, v), (0.7 + 0.01 * lam) * v, atol=1e-12 * lam)
+
+
+@pytest.mark.parametrize("shape,comp", [((8, 8), 0), ((8, 8), 1), ((4, 8, 8), 0), ((4, 8, 8), 2)])
+def test_face_sweep_zeroes_residual_on_each_set(shape, comp):
+    h = 1.0 / shape[-1]
+    op = st.FaceOperator(shape, h, 1.0, 0.05, comp)
+    u = random_field(shape, 801)
+    u[st.frozen_slice(op)] = 0.0
+    f = random_field(shape, 802, -1, 1)
+    f[st.frozen_slice(op)] = 0.0
+    sets = cc.SETS_2D if len(shape) == 2 else cc.SETS_3D
+    for par in sets:
+        # one set only: emulate by a full sweep restricted to that set
+        pad_before = u.copy()
+        orig_sets = cc.SETS_2D, cc.SETS_3D
+        try:
+            cc.SETS_2D = (par,) if len(shape) == 2 else cc.SETS_2D
+            cc.SETS_3D = (par,) if len(shape) == 3 else cc.SETS_3D
+            st.xmcgs_sweep_face(op, u, f)
+        finally:
+            cc.SETS_2D, cc.SETS_3D = orig_sets
+        _, cell = cc._set_slices(op, par)
+        r = st.residual_face(op, u, f)
+        assert np.max(np.abs(r[cell])) < 1e-12 * (np.max(np.abs(f)) + np.max(np.abs(st.apply_A_face(op, u))))
+        assert not np.array_equal(pad_before, u)
+    assert np.all(u[st.frozen_slice(op)] == 0.0)
+
+
+@pytest.mark.parametrize("shape,comp", [((16, 16), 0), ((16, 16), 1), ((8, 8, 8), 1)])
+def test_face_transfers_exact_on_linear_fields(shape, comp):
+    dim = len(shape)
+    h = 1.0 / shape[-1]
+    op = st.FaceOperator(shape, h, 1.0, 1.0, comp)
+    fax = op.fax
+    coef = [0.3, -1.2, 0.7][:dim]
+
+    def field(shp, hh):
+        out = np.full(shp, 0.5)
+        for ax in range(dim):
+            n = shp[ax]
+            x = (np.arange(n) + 1.0) * hh if ax == fax else (np.arange(n) + 0.5) * hh
+            sh = [1] * dim
+            sh[ax] = n
+            out = out + coef[ax] * x.reshape(sh)
+        return out
+
+    fine, coarse = field(shape, h), field(tuple(n // 2 for n in shape), 2 * h)
+    rc = st.restrict_face(op, fine)
+    sl = [slice(None)] * dim
+    sl[fax] = slice(0, shape[fax] // 2 - 1)
+    np.testing.assert_allclose(rc[tuple(sl)], coarse[tuple(sl)], rtol=0, atol=1e-13)
+    assert np.all(rc[st.frozen_slice(st.FaceOperator(tuple(n // 2 for n in shape), 2 * h, 1, 1, comp))] == 0)
+    pf = st.prolong_face(op, coarse)
+    # interior: away from the tangential walls and from both normal walls (fine faces 1 and n-1 sit
+    # next to a wall face, whose value 0 enters their average)
+    sl = [slice(1, -1)] * dim
+    sl[fax] = slice(1, shape[fax] - 2)
+    np.testing.assert_allclose(pf[tuple(sl)], fine[tuple(sl)], rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("shape,comp", [((16, 16), 0), ((8, 16), 1), ((8, 8, 8), 2)])
+def test_face_vcycle_converges_to_dense_solution(shape, comp):
+    h = 1.0 / shape[-1]
+    op = st.FaceOperator(shape, h, 1.0, 0.02, comp)
+    f = random_field(shape, 811, -1, 1)
+    f[st.frozen_slice(op)] = 0.0
+    u = np.zeros(shape)
+    info = st.solve_face(st.build_levels_face(op, 2), u, f, cc.Params(tol=1e-14, kmax=60, coarsest=2))
+    assert info.converged
+    M = st.dense_matrix_face(op)
+    keep = np.ones(shape, bool)
+    keep[st.frozen_slice(op)] = False
+    idx = np.where(keep.ravel())[0]
+    exact = np.zeros(int(np.prod(shape)))
+    exact[idx] = np.linalg.solve(M[np.ix_(idx, idx)], f.ravel()[idx])
+    np.testing.assert_allclose(u.ravel(), exact, atol=1e-12 * np.max(np.abs(exact)))
+
+
+def test_weno3_exact_on_linear_fields_and_constant_flow():
+    """Away from walls, WENO3 reproduces the derivative of a linear field exactly, and a constant
+    advected field has zero convection."""
+    shape = (16, 16)
+    h = 1.0 / 16
+    x = (np.arange(16) + 0.5) * h
+    phi = np.tile(2.0 + 3.0 * x, (16, 1))  # linear along x (numpy axis 1), cells
+    dm, dp = st.weno3_derivatives(phi, 1, h, False, 0.0, 0.0)
+    np.testing.assert_allclose(dm[:, 2:-2], 3.0, atol=1e-12)
+    np.testing.assert_allclose(dp[:, 2:-2], 3.0, atol=1e-12)
+    xf = (np.arange(16) + 1.0) * h
+    u = np.tile(np.where(np.arange(16) < 15, 1.0 + 0.5 * xf, 0.0), (16, 1))
+    dm, dp = st.weno3_derivatives(u, 1, h, True, 0.0, 0.0)
+    np.testing.assert_allclose(dm[:, 2:-3], 0.5, atol=1e-12)
+    np.testing.assert_allclose(dp[:, 2:-3], 0.5, atol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_projection_step_divergence_free(dim):
+    n = 16
+    shape = (n,) * dim
+    h = 1.0 / n
+    names = ["U", "V", "W"][:dim]
+    fields = {}
+    for k, nm in enumerate(names):
+        op = st.FaceOperator(shape, h, 1.0, 1.0, k)
+        v = 0.1 * random_field(shape, 820 + k, -1, 1)
+        v[st.frozen_slice(op)] = 0.0
+        fields[nm + "_old"] = v
+        fields[nm + "_new"] = np.zeros(shape)
+    fields["P_old"] = np.zeros(shape)
+    fields["P_new"] = np.zeros(shape)
+    prm = st.NSParams(Re=100.0, dt=1e-2, lid=(1.0, 0.0, 0.0),
+                      solver=cc.Params(tol=1e-12, kmax=60, coarsest=2),
+                      pressure=cc.Params(tol=1e-12, kmax=200, coarsest=2, coarse_exact=True))
+    for _ in range(2):
+        infos, div, rhs = st.projection_step(fields, shape, h, prm)
+        assert all(i.converged for i in infos)
+        assert div <= 1e-9 * max(rhs, 1.0)
+    # the lid drags the fluid next to it in +x
+    assert fields["U_old"][-1].mean() > 0

@@ -48,6 +48,16 @@ typedef enum {
 typedef enum { FAS_BC_NEUMANN = 0, FAS_BC_DIRICHLET = 1 } fas_bc;
 typedef enum { FAS_FP64 = 0, FAS_MIXED = 1 } fas_precision;
 
+/* Where the unknowns sit (Sec. 4.1, the MAC staggered grid). FAS_CELL: cell centres (Sec. 2.1).
+ * FAS_FACE_X / _Y / _Z: one velocity component on the faces normal to x / y / z. A face field has
+ * the cell-field shape: along its own axis, slot s holds face s+1 (faces 1..n-1 are the unknowns)
+ * and the last slot holds the far wall face, whose value is 0 and is never changed; the near wall
+ * face is not stored and is 0. Every wall is no-slip: the normal component is 0 on its own walls,
+ * tangential walls act as homogeneous Dirichlet ghosts (ghost = -adjacent value, Sec. 4.1), so bc[]
+ * must be all FAS_BC_DIRICHLET. Smoothing uses the X-MCGS sets by the parity of the face index and
+ * the cell indices (Eqs. FCGS-1..4 on faces); restriction and prolongation are those of Appendix D. */
+typedef enum { FAS_CELL = 0, FAS_FACE_X = 1, FAS_FACE_Y = 2, FAS_FACE_Z = 3 } fas_location;
+
 /* Problem and solver parameters (the paper's user parameters s, kMax, tol, meshLevel of
  * Algorithm 1's symbol table, plus the operator of Sec. 2.2 generalised to alpha, beta, kappa). */
 typedef struct {
@@ -71,6 +81,8 @@ typedef struct {
   int path;              /* 0: sweep-fused kernels where the level allows (default);
                           * 1: one kernel per operation everywhere (reference path)           */
   int seg_rows;          /* rows per warp segment in the fused 2D kernels (0: default 128)      */
+  int location;          /* fas_location (default FAS_CELL). Face grids need kappa == NULL and
+                          * coarse_exact 0; they run the per-operation kernels                  */
 } fas_params;
 
 /* Per-solve report. res0/res are ||f - A u||_2 before the first and after the last cycle
@@ -170,10 +182,12 @@ fas_status fas_residual(fas_ctx* ctx, int level, const double* u, const double* 
 /* `sweeps` X-MCGS sweeps in place on u of level `level` (Sec. 2.3 / Appendix B). */
 fas_status fas_smooth(fas_ctx* ctx, int level, double* u, const double* f, int sweeps);
 
-/* uc = R(u) (Appendix C average of 2^d children), u of level `level`, uc of level + 1. */
+/* uc = R(u) (Appendix C average of 2^d children; on a face grid the Appendix D face restriction),
+ * u of level `level`, uc of level + 1. */
 fas_status fas_restrict(fas_ctx* ctx, int level, const double* u, double* uc);
 
-/* u += P(c) (Appendix C piecewise-constant prolongation), c of level + 1, u of level `level`. */
+/* u += P(c) (Appendix C piecewise-constant prolongation; on a face grid the Appendix D face
+ * prolongation), c of level + 1, u of level `level`. */
 fas_status fas_prolong_add(fas_ctx* ctx, int level, double* u, const double* c);
 
 /* --- kernel timing (CUDA events on the context's stream) ------------------------------------ */

@@ -31,6 +31,7 @@ STATUS_NAMES = ["FAS_OK", "FAS_EINVAL", "FAS_ENOMEM", "FAS_ENOTCONV", "FAS_ENONF
                 "FAS_ECUDA", "FAS_EUNSUPPORTED"]
 FAS_BC_NEUMANN, FAS_BC_DIRICHLET = 0, 1
 FAS_FP64, FAS_MIXED = 0, 1
+FAS_CELL, FAS_FACE_X, FAS_FACE_Y, FAS_FACE_Z = 0, 1, 2, 3
 
 
 class fas_params(ctypes.Structure):
@@ -42,6 +43,7 @@ class fas_params(ctypes.Structure):
         ("coarsest", ctypes.c_int), ("coarse_exact", ctypes.c_int), ("tol", ctypes.c_double),
         ("tol_relative", ctypes.c_int), ("precision", ctypes.c_int), ("inner_cycles", ctypes.c_int),
         ("use_graph", ctypes.c_int), ("path", ctypes.c_int), ("seg_rows", ctypes.c_int),
+        ("location", ctypes.c_int),
     ]
 
 
@@ -105,6 +107,11 @@ def load(path: str | None = None):
         "fas_autotune": (_I, [_P, _P, _P, ctypes.POINTER(fas_tune_result)]),
         "fas_heat_adjoint": (_I, [_P, _P, _P, _D, _I, _P, _P, _P, _P, _P, _I]),
         "fas_prof_read": (_I, [_P, ctypes.c_void_p, _I, ctypes.POINTER(_I)]),
+        "ns_create": (_I, [_I, ctypes.POINTER(_I), _D, _D, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(fas_params),
+                           ctypes.POINTER(fas_params), _P, ctypes.POINTER(_P)]),
+        "ns_projection_step": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(fas_info), ctypes.POINTER(_D)]),
+        "ns_launch_count": (ctypes.c_longlong, [_P, _I]),
+        "ns_destroy": (_I, [_P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -307,6 +314,65 @@ def fas_autotune(ctx: _Ctx, u_scratch, f) -> dict:
 
 def fas_launch_count(ctx: _Ctx, reset: bool = False) -> int:
     return load().fas_launch_count(ctx.handle, 1 if reset else 0)
+
+
+class _NsCtx:
+    """Owns an ns_ctx* (projection step on the MAC grid) and its grid shape (numpy order)."""
+
+    def __init__(self, handle, shape):
+        self.handle = handle
+        self.shape = tuple(shape)
+        self.cells = 1
+        for v in shape:
+            self.cells *= int(v)
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.ns_destroy(self.handle)
+            self.handle = None
+
+
+NS_FIELDS = ("U_new", "U_old", "V_new", "V_old", "W_new", "W_old", "P_new", "P_old")
+
+
+def ns_create(shape, h: float, Re: float, dt: float, lid=(1.0, 0.0, 0.0), order: int = 1, solver=None,
+              pressure=None, stream=None) -> _NsCtx:
+    """ns_create for a numpy-order shape ((ny, nx) or (nz, ny, nx)); solver / pressure are fas_params
+    (None: the library's defaults)."""
+    lib = load()
+    dim = len(shape)
+    phys = list(reversed([int(v) for v in shape])) + [1] * (3 - dim)
+    n = (_I * 3)(*phys)
+    lid3 = (_D * 3)(*(list(lid) + [0.0] * 3)[:3])
+    out = _P()
+    sp = ctypes.byref(solver) if solver is not None else None
+    pp = ctypes.byref(pressure) if pressure is not None else None
+    _check(lib.ns_create(dim, n, float(h), float(Re), float(dt), int(order), lid3, sp, pp, _stream_handle(stream),
+                         ctypes.byref(out)), "ns_create")
+    return _NsCtx(out, shape)
+
+
+def ns_projection_step(ns: _NsCtx, fields: dict, want_div: bool = True, allow_notconv: bool = False):
+    """One projection step on the eight resident fields (dict of float64 CUDA tensors named as in
+    NS_FIELDS; W_* absent in 2D). Returns (infos[4], max |div u^{n+1}| or None)."""
+    n = ns.cells
+    ptrs = (_P * 8)(*[_dev(fields.get(k), k, n) for k in NS_FIELDS])
+    infos = (fas_info * 4)()
+    dmax = _D(0.0)
+    st = load().ns_projection_step(ns.handle, ptrs, infos, ctypes.byref(dmax) if want_div else None)
+    if not (allow_notconv and st == FAS_ENOTCONV):
+        _check(st, "ns_projection_step")
+    return [infos[k] for k in range(4)], (dmax.value if want_div else None)
+
+
+def ns_launch_count(ns: _NsCtx, reset: bool = False) -> int:
+    return int(load().ns_launch_count(ns.handle, 1 if reset else 0))
+
+
+def ns_destroy(ns: _NsCtx) -> None:
+    if ns.handle:
+        _check(load().ns_destroy(ns.handle), "ns_destroy")
+        ns.handle = None
 
 
 class fas_prof_record(ctypes.Structure):

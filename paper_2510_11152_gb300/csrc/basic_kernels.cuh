@@ -25,6 +25,7 @@ __device__ __forceinline__ void smooth_colour_range(T* u, const T* f, const Leve
     const int l = (int)(t >> (lhx + L.ly));
     const int i = 2 * k + ((colour + DIM + j + l) & 1);
     const int64_t idx = ((int64_t)l * L.ny + j) * L.nx + i;
+    if (L.fax >= 0 && frozen(L, i, j, l)) continue;
     u[idx] = point_update<T, DIM>(u, f, L, idx, i, j, l);
   }
 }
@@ -40,7 +41,7 @@ __device__ __forceinline__ float residual_range(T* r, const T* u, const T* f, co
     const int i = (int)(idx & (L.nx - 1));
     const int j = (int)((idx >> L.lx) & (L.ny - 1));
     const int l = (int)(idx >> (L.lx + L.ly));
-    const T rv = residual_point<T, DIM>(u, f, L, idx, i, j, l);
+    const T rv = (L.fax >= 0 && frozen(L, i, j, l)) ? T(0) : residual_point<T, DIM>(u, f, L, idx, i, j, l);
     if (r) r[idx] = rv;
     const float rs = (float)rv * nscale;
     acc = fmaf(rs, rs, acc);
@@ -90,6 +91,7 @@ __device__ __forceinline__ void tau_range(T* fc, const T* uc, const LevelDesc<T>
     const int i = (int)(idx & (Lc.nx - 1));
     const int j = (int)((idx >> Lc.lx) & (Lc.ny - 1));
     const int l = (int)(idx >> (Lc.lx + Lc.ly));
+    if (Lc.fax >= 0 && frozen(Lc, i, j, l)) continue;
     fc[idx] = fc[idx] + apply_point<T, DIM>(uc, Lc, idx, i, j, l);
   }
 }
@@ -120,6 +122,129 @@ __device__ __forceinline__ void prolong_range(T* u, const T* uc, const T* uc0, i
     }
   }
 }
+
+// ---- Appendix D transfers for face grids. FAX is the index axis normal to the faces (0 x, 1 y,
+// 2 z); slot s along it is face s+1, the last slot the far wall (0), the near wall face is 0.
+// Restriction: coarse slot S = fine slots 2S, 2S+1, 2S+2 weighted 1/4, 1/2, 1/4, times the average
+// of the two fine cells along each tangential axis; the coarse wall slot is 0.
+template <typename T, int DIM, int FAX, typename Get>
+__device__ __forceinline__ T face_avg_of(Get get, int ic, int jc, int lc, int nxf, int nyf) {
+  const int c3[3] = {ic, jc, lc};
+  T acc = T(0);
+#pragma unroll
+  for (int w = 0; w < 3; ++w) {
+    T s = T(0);
+#pragma unroll
+    for (int t = 0; t < (DIM == 3 ? 4 : 2); ++t) {
+      int f3[3] = {0, 0, 0};
+      int tb = 0;  // tangential bit
+#pragma unroll
+      for (int ax = 0; ax < DIM; ++ax) {
+        if (ax == FAX) {
+          f3[ax] = 2 * c3[ax] + w;
+        } else {
+          f3[ax] = 2 * c3[ax] + ((t >> tb) & 1);
+          ++tb;
+        }
+      }
+      s += get(((int64_t)f3[2] * nyf + f3[1]) * nxf + f3[0], f3[0], f3[1], f3[2]);
+    }
+    acc += (w == 1 ? T(0.5) : T(0.25)) * s;
+  }
+  return acc * (DIM == 3 ? T(0.25) : T(0.5));
+}
+
+template <typename T, int DIM, int FAX>
+__device__ __forceinline__ T face_avg(const T* v, int ic, int jc, int lc, int nxf, int nyf) {
+  return face_avg_of<T, DIM, FAX>([v](int64_t q, int, int, int) { return v[q]; }, ic, jc, lc, nxf, nyf);
+}
+
+template <int FAX>
+__device__ __forceinline__ bool wall_slot(int i, int j, int l, int nx, int ny, int nz) {
+  return FAX == 0 ? i == nx - 1 : (FAX == 1 ? j == ny - 1 : l == nz - 1);
+}
+
+template <typename T, int DIM, int FAX>
+__device__ __forceinline__ void restrict_face_range(T* uc, T* uc0, T* fc, const T* u, const T* r, int nxf, int nyf,
+                                                    int nzf, int64_t t0, int64_t stride) {
+  const int nxc = nxf >> 1, nyc = nyf >> 1, nzc = DIM == 3 ? nzf >> 1 : 1;
+  const int64_t nc = (int64_t)nxc * nyc * nzc;
+  const int lxc = __ffs(nxc) - 1, lyc = __ffs(nyc) - 1;
+  for (int64_t I = t0; I < nc; I += stride) {
+    const int ic = (int)(I & (nxc - 1));
+    const int jc = (int)((I >> lxc) & (nyc - 1));
+    const int lc = (int)(I >> (lxc + lyc));
+    const bool wall = wall_slot<FAX>(ic, jc, lc, nxc, nyc, nzc);
+    if (u) {
+      const T v = wall ? T(0) : face_avg<T, DIM, FAX>(u, ic, jc, lc, nxf, nyf);
+      uc[I] = v;
+      if (uc0) uc0[I] = v;
+    }
+    if (r) fc[I] = wall ? T(0) : face_avg<T, DIM, FAX>(r, ic, jc, lc, nxf, nyf);
+  }
+}
+
+// Prolongation of the correction c = uc - uc0 (c = uc without uc0), added to every fine slot but
+// the wall slot. Along each tangential axis the fine cell 2J takes (3 c_J + c_{J-1})/4 and 2J+1 takes
+// (3 c_J + c_{J+1})/4, the coarse ghost beyond a wall being -c_J (no-slip walls). Along the face axis
+// the odd fine slot 2S+1 coincides with coarse slot S; the even slot 2S lies halfway between coarse
+// slots S-1 and S (slot -1 is the near wall, 0).
+template <typename T, int DIM, int FAX>
+__device__ __forceinline__ void prolong_face_range(T* u, const T* uc, const T* uc0, int nxf, int nyf, int nzf,
+                                                   int64_t t0, int64_t stride) {
+  const int nxc = nxf >> 1, nyc = nyf >> 1, nzc = DIM == 3 ? nzf >> 1 : 1;
+  const int64_t n = (int64_t)nxf * nyf * nzf;
+  const int lx = __ffs(nxf) - 1, ly = __ffs(nyf) - 1;
+  for (int64_t idx = t0; idx < n; idx += stride) {
+    const int f3[3] = {(int)(idx & (nxf - 1)), (int)((idx >> lx) & (nyf - 1)), DIM == 3 ? (int)(idx >> (lx + ly)) : 0};
+    const int nf3[3] = {nxf, nyf, nzf};
+    const int nc3[3] = {nxc, nyc, nzc};
+    if (f3[FAX] == nf3[FAX] - 1) continue;
+    int cp[3][2];
+    T cw[3][2];
+    int cnt[3] = {1, 1, 1};
+    cp[2][0] = 0;
+    cw[2][0] = T(1);
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      const int fi = f3[ax], C = fi >> 1;
+      if (ax == FAX) {
+        if (fi & 1) {
+          cp[ax][0] = C;
+          cw[ax][0] = T(1);
+        } else {
+          // coarse slots C - 1 and C, each with weight 1/2 unless it is a wall (slot -1, or the
+          // coarse wall slot nc - 1): a wall face contributes 0
+          const bool lo = C >= 1, hi = C < nc3[ax] - 1;
+          cp[ax][0] = hi ? C : C - 1;
+          cw[ax][0] = (hi || lo) ? T(0.5) : T(0);
+          cp[ax][1] = C - 1;
+          cw[ax][1] = T(0.5);
+          cnt[ax] = (hi && lo) ? 2 : 1;
+          if (!hi && !lo) cp[ax][0] = 0;
+        }
+      } else {
+        const int nb = (fi & 1) ? C + 1 : C - 1;
+        const bool ghost = nb < 0 || nb >= nc3[ax];
+        cp[ax][0] = C;
+        cw[ax][0] = T(0.75);
+        cp[ax][1] = ghost ? C : nb;
+        cw[ax][1] = ghost ? T(-0.25) : T(0.25);
+        cnt[ax] = 2;
+      }
+    }
+    T acc = T(0);
+    for (int a0 = 0; a0 < cnt[0]; ++a0)
+      for (int a1 = 0; a1 < cnt[1]; ++a1)
+        for (int a2 = 0; a2 < cnt[2]; ++a2) {
+          const int64_t I = ((int64_t)cp[2][a2] * nyc + cp[1][a1]) * nxc + cp[0][a0];
+          const T cv = uc0 ? uc[I] - uc0[I] : uc[I];
+          acc += (cw[0][a0] * cw[1][a1] * cw[2][a2]) * cv;
+        }
+    u[idx] += acc;
+  }
+}
+
 
 // ------------------------------------------------------------------------------------------------
 // grid-stride kernels
@@ -172,6 +297,16 @@ __global__ void k_prolong(T* u, const T* uc, const T* uc0, int nxf, int nyf, int
   prolong_range<T, DIM>(u, uc, uc0, nxf, nyf, nzf, gtid(), gstride());
 }
 
+template <typename T, int DIM, int FAX>
+__global__ void k_restrict_face(T* uc, T* uc0, T* fc, const T* u, const T* r, int nxf, int nyf, int nzf) {
+  restrict_face_range<T, DIM, FAX>(uc, uc0, fc, u, r, nxf, nyf, nzf, gtid(), gstride());
+}
+
+template <typename T, int DIM, int FAX>
+__global__ void k_prolong_face(T* u, const T* uc, const T* uc0, int nxf, int nyf, int nzf) {
+  prolong_face_range<T, DIM, FAX>(u, uc, uc0, nxf, nyf, nzf, gtid(), gstride());
+}
+
 // per-block partial sums of x (for means of singular problems)
 template <typename T>
 __global__ void k_sum(const T* x, int64_t n, double* partials) {
@@ -217,7 +352,7 @@ __global__ void k_ir_residual(float* r32, const double* u, const double* b, Leve
     const int i = (int)(idx & (L.nx - 1));
     const int j = (int)((idx >> L.lx) & (L.ny - 1));
     const int l = (int)(idx >> (L.lx + L.ly));
-    const float rv = (float)residual_point<double, DIM>(u, b, L, idx, i, j, l);
+    const float rv = (L.fax >= 0 && frozen(L, i, j, l)) ? 0.f : (float)residual_point<double, DIM>(u, b, L, idx, i, j, l);
     r32[idx] = rv;
     const float rs = rv * nscale;
     acc = fmaf(rs, rs, acc);
@@ -366,7 +501,33 @@ __device__ __forceinline__ void restrict_resid_range(T* uc, T* uc0, T* fc, const
   }
 }
 
-template <typename T, int DIM>
+// Face-grid counterpart: the fine residual is evaluated at each fine face the Appendix D weights
+// touch (the three normal slots overlap between neighbouring coarse faces, so some are evaluated
+// twice); the arithmetic per value equals that of k_residual followed by k_restrict_face.
+template <typename T, int DIM, int FAX>
+__device__ __forceinline__ void restrict_resid_face_range(T* uc, T* uc0, T* fc, const T* u, const T* f,
+                                                          const LevelDesc<T>& L, int64_t t0, int64_t stride) {
+  const int nxf = L.nx, nyf = L.ny;
+  const int nxc = nxf >> 1, nyc = nyf >> 1, nzc = DIM == 3 ? L.nz >> 1 : 1;
+  const int64_t nc = (int64_t)nxc * nyc * nzc;
+  const int lxc = L.lx - 1, lyc = L.ly - 1;
+  auto resid = [&](int64_t q, int i, int j, int l) {
+    return frozen(L, i, j, l) ? T(0) : residual_point<T, DIM>(u, f, L, q, i, j, l);
+  };
+  for (int64_t I = t0; I < nc; I += stride) {
+    const int ic = (int)(I & (nxc - 1));
+    const int jc = (int)((I >> lxc) & (nyc - 1));
+    const int lc = (int)(I >> (lxc + lyc));
+    const bool wall = wall_slot<FAX>(ic, jc, lc, nxc, nyc, nzc);
+    const T v = wall ? T(0) : face_avg<T, DIM, FAX>(u, ic, jc, lc, nxf, nyf);
+    uc[I] = v;
+    uc0[I] = v;
+    fc[I] = wall ? T(0) : face_avg_of<T, DIM, FAX>(resid, ic, jc, lc, nxf, nyf);
+  }
+}
+
+// FAX = -1: cell-centred levels; 0..2: face grids normal to that index axis.
+template <typename T, int DIM, int FAX>
 __global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayout S, T* utop, const T* ftop) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -394,8 +555,12 @@ __global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayou
     T* u = sm + S.off_u[l];
     const T* f = sm + S.off_f[l];
     coarse_smooth<T, DIM>(u, f, L, A.nu1);
-    restrict_resid_range<T, DIM>(sm + S.off_u[l + 1], sm + S.off_u0[l + 1], sm + S.off_f[l + 1], u, f, L,
-                                 threadIdx.x, blockDim.x);
+    if constexpr (FAX < 0)
+      restrict_resid_range<T, DIM>(sm + S.off_u[l + 1], sm + S.off_u0[l + 1], sm + S.off_f[l + 1], u, f, L,
+                                   threadIdx.x, blockDim.x);
+    else
+      restrict_resid_face_range<T, DIM, FAX>(sm + S.off_u[l + 1], sm + S.off_u0[l + 1], sm + S.off_f[l + 1], u, f,
+                                             L, threadIdx.x, blockDim.x);
     __syncthreads();
     tau_range<T, DIM>(sm + S.off_f[l + 1], sm + S.off_u[l + 1], sdesc[l + 1], threadIdx.x, blockDim.x);
     __syncthreads();
@@ -421,7 +586,11 @@ __global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayou
     const LevelDesc<T>& L = sdesc[l];
     T* u = sm + S.off_u[l];
     const T* f = sm + S.off_f[l];
-    prolong_range<T, DIM>(u, sm + S.off_u[l + 1], sm + S.off_u0[l + 1], L.nx, L.ny, L.nz, threadIdx.x, blockDim.x);
+    if constexpr (FAX < 0)
+      prolong_range<T, DIM>(u, sm + S.off_u[l + 1], sm + S.off_u0[l + 1], L.nx, L.ny, L.nz, threadIdx.x, blockDim.x);
+    else
+      prolong_face_range<T, DIM, FAX>(u, sm + S.off_u[l + 1], sm + S.off_u0[l + 1], L.nx, L.ny, L.nz, threadIdx.x,
+                                      blockDim.x);
     __syncthreads();
     coarse_smooth<T, DIM>(u, f, L, A.nu2);
   }

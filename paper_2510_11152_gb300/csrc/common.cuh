@@ -28,6 +28,9 @@ struct LevelDesc {
   int nx, ny, nz;  // cells per axis (nz = 1 in 2D), powers of two
   int lx, ly, lz;  // their base-2 logarithms (index decomposition by shifts)
   int varkappa;    // 1: use the per-cell arrays below
+  int fax;         // -1: cell-centred unknowns; 0/1/2: face unknowns normal to x/y/z (staggered
+                   // velocity component): slot s of that axis is face s+1, the last slot is the
+                   // far wall (frozen at 0), the near wall face is implicit and 0
   T h2, ih2;       // h^2, 1/h^2
   T c;             // beta kappa / h^2 (constant kappa)
   const T* wx;     // beta kappa_f of the face between cells i and i+1, stored at cell i (0 at i = nx-1)
@@ -44,6 +47,12 @@ __device__ __forceinline__ int bclass(int i, int j, int l, int nx, int ny, int n
   int fl = (i == 0) | ((i == nx - 1) << 1) | ((j == 0) << 2) | ((j == ny - 1) << 3);
   if (DIM == 3) fl |= ((l == 0) << 4) | ((l == nz - 1) << 5);
   return fl;
+}
+
+// True for the frozen wall slot of a face grid (never updated, residual 0).
+template <typename T>
+__device__ __forceinline__ bool frozen(const LevelDesc<T>& L, int i, int j, int l) {
+  return (L.fax == 0 && i == L.nx - 1) || (L.fax == 1 && j == L.ny - 1) || (L.fax == 2 && l == L.nz - 1);
 }
 
 // Sum of the existing neighbours of cell (i, j, l) at linear index idx (constant kappa).

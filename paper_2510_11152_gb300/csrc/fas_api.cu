@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "basic_kernels.cuh"
@@ -114,6 +115,7 @@ LevelDesc<T> make_desc(const fas_params& p, const LevelShape& s) {
   L.ly = lg(s.ny);
   L.lz = lg(s.nz);
   L.varkappa = p.kappa != nullptr;
+  L.fax = p.location - 1;  // FAS_CELL -> -1, FAS_FACE_X/Y/Z -> 0/1/2
   const double h2 = s.h * s.h;
   L.h2 = (T)h2;
   L.ih2 = (T)(1.0 / h2);
@@ -124,7 +126,10 @@ LevelDesc<T> make_desc(const fas_params& p, const LevelShape& s) {
     double m = 0.0;
     for (int face = 0; face < nfaces; ++face) {
       const bool boundary = (cls >> face) & 1;
-      m += boundary ? bc_mult(p.bc[face]) : 1.0;
+      // face grid, own axis: the near wall face is a neighbour of value 0 (weight 1); the far one is
+      // stored (the frozen slot), so only the near side is ever a boundary of an unknown
+      const double mb = face / 2 == L.fax ? 1.0 : bc_mult(p.bc[face]);
+      m += boundary ? mb : 1.0;
     }
     const double D = p.alpha * h2 + bk * m;
     L.a[cls] = (T)(D != 0.0 ? bk / D : 0.0);
@@ -355,7 +360,8 @@ fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers)
     // sweep-fused 2D path (float32 only): consecutive levels from the finest that the fused kernels
     // handle and that are larger than the single-CTA switch level
     H.nfast = 0;
-    if (sizeof(T) == 4 && p.dim == 2 && p.path == 0 && !p.kappa && p.nu1 >= 1 && p.nu2 >= 1) {
+    if (sizeof(T) == 4 && p.dim == 2 && p.path == 0 && !p.kappa && p.location == FAS_CELL && p.nu1 >= 1 &&
+        p.nu2 >= 1) {
       while (H.nfast < H.switch_level &&
              stream2d_supported(c->shape[H.nfast].nx, c->shape[H.nfast].ny, std::max(p.nu1, p.nu2)))
         H.nfast++;
@@ -393,6 +399,42 @@ fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers)
 // ---------------------------------------------------------------------------------------------
 // launches
 // ---------------------------------------------------------------------------------------------
+
+// Calls fn(std::integral_constant<int, FAX>) for the context's unknown location (FAX = -1 cells,
+// 0..2 faces normal to x, y, z).
+template <typename F>
+void with_fax(const fas_ctx* c, F&& fn) {
+  switch (c->p.location) {
+    case FAS_FACE_X: fn(std::integral_constant<int, 0>()); break;
+    case FAS_FACE_Y: fn(std::integral_constant<int, 1>()); break;
+    case FAS_FACE_Z: fn(std::integral_constant<int, 2>()); break;
+    default: fn(std::integral_constant<int, -1>()); break;
+  }
+}
+
+// u (and u0) at level+1 from u, f at level+1 from r: Appendix C on cells, Appendix D on faces.
+template <typename T, int DIM>
+void launch_restrict(fas_ctx* c, int64_t nc, T* uc, T* uc0, T* fc, const T* u, const T* r, int nx, int ny, int nz) {
+  with_fax(c, [&](auto tag) {
+    constexpr int FAX = decltype(tag)::value;
+    if constexpr (FAX < 0)
+      k_restrict<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(uc, uc0, fc, u, r, nx, ny, nz);
+    else
+      k_restrict_face<T, DIM, FAX><<<grid_for(c, nc), kBlock, 0, c->stream>>>(uc, uc0, fc, u, r, nx, ny, nz);
+  });
+}
+
+// u += P(uc - uc0) (uc0 may be null), u of a level with n cells.
+template <typename T, int DIM>
+void launch_prolong(fas_ctx* c, int64_t n, T* u, const T* uc, const T* uc0, int nx, int ny, int nz) {
+  with_fax(c, [&](auto tag) {
+    constexpr int FAX = decltype(tag)::value;
+    if constexpr (FAX < 0)
+      k_prolong<T, DIM><<<grid_for(c, n >> DIM), kBlock, 0, c->stream>>>(u, uc, uc0, nx, ny, nz);
+    else
+      k_prolong_face<T, DIM, FAX><<<grid_for(c, n), kBlock, 0, c->stream>>>(u, uc, uc0, nx, ny, nz);
+  });
+}
 
 template <typename T, int DIM>
 void launch_smooth(fas_ctx* c, const LevelDesc<T>& L, int level, T* u, const T* f, int sweeps) {
@@ -441,7 +483,9 @@ fas_status launch_coarse(fas_ctx* c, Hier<T>& H, int l0, T* utop, const T* ftop)
   A.nu2 = p.nu2;
   A.nuc = p.nu_coarse > 0 ? p.nu_coarse : p.nu1;
   Prof pr(c, FAS_K_COARSE, l0, (double)c->shape[l0].cells());
-  k_coarse_smem<T, DIM><<<1, kCoarseThreads, H.smem_bytes, c->stream>>>(A, H.smem, utop, ftop);
+  with_fax(c, [&](auto tag) {
+    k_coarse_smem<T, DIM, decltype(tag)::value><<<1, kCoarseThreads, H.smem_bytes, c->stream>>>(A, H.smem, utop, ftop);
+  });
   return FAS_OK;
 }
 
@@ -464,8 +508,7 @@ fas_status vcycle_basic_from(fas_ctx* c, Hier<T>& H, int lfrom, T* utop, const T
     const int64_t nc = n >> DIM;
     {
       Prof pr(c, FAS_K_RESTRICT, l, (double)n);
-      k_restrict<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.u[l + 1], H.u0[l + 1], H.f[l + 1], u,
-                                                                    H.r[l], L.nx, L.ny, L.nz);
+      launch_restrict<T, DIM>(c, nc, H.u[l + 1], H.u0[l + 1], H.f[l + 1], u, H.r[l], L.nx, L.ny, L.nz);
     }
     {
       Prof pr(c, FAS_K_TAU, l + 1, (double)nc);
@@ -480,8 +523,7 @@ fas_status vcycle_basic_from(fas_ctx* c, Hier<T>& H, int lfrom, T* utop, const T
     const int64_t n = (int64_t)L.nx * L.ny * L.nz;
     {
       Prof pr(c, FAS_K_PROLONG, l, (double)n);
-      k_prolong<T, DIM><<<grid_for(c, n >> DIM), kBlock, 0, c->stream>>>(u, H.u[l + 1], H.u0[l + 1], L.nx, L.ny,
-                                                                         L.nz);
+      launch_prolong<T, DIM>(c, n, u, H.u[l + 1], H.u0[l + 1], L.nx, L.ny, L.nz);
     }
     launch_smooth<T, DIM>(c, L, l, u, f, p.nu2);
   }
@@ -985,6 +1027,22 @@ void fasmg::set_last_error(const std::string& msg) { g_last_error = msg; }
 // C ABI
 // =============================================================================================
 
+// The single-CTA kernel's dynamic shared memory limit, for every unknown location.
+template <typename T, int DIM>
+cudaError_t coarse_attr() {
+  cudaError_t e = cudaSuccess;
+  for (cudaError_t ek : {cudaFuncSetAttribute(k_coarse_smem<T, DIM, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kCoarseSmemLimit),
+                         cudaFuncSetAttribute(k_coarse_smem<T, DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kCoarseSmemLimit),
+                         cudaFuncSetAttribute(k_coarse_smem<T, DIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kCoarseSmemLimit),
+                         cudaFuncSetAttribute(k_coarse_smem<T, DIM, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kCoarseSmemLimit)})
+    if (e == cudaSuccess) e = ek;
+  return e;
+}
+
 extern "C" {
 
 void fas_default_params(fas_params* p) {
@@ -1011,6 +1069,7 @@ void fas_default_params(fas_params* p) {
   p->use_graph = 1;
   p->path = 0;
   p->seg_rows = 0;
+  p->location = FAS_CELL;
 }
 
 fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
@@ -1030,6 +1089,13 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
   if (p.precision != FAS_FP64 && p.precision != FAS_MIXED) return fail(FAS_EINVAL, "unknown precision");
   for (int k = 0; k < 2 * p.dim; ++k)
     if (p.bc[k] != FAS_BC_NEUMANN && p.bc[k] != FAS_BC_DIRICHLET) return fail(FAS_EINVAL, "unknown bc kind");
+  if (p.location < FAS_CELL || p.location > p.dim) return fail(FAS_EINVAL, "location must be a cell or a face axis");
+  if (p.location != FAS_CELL) {
+    for (int k = 0; k < 2 * p.dim; ++k)
+      if (p.bc[k] != FAS_BC_DIRICHLET) return fail(FAS_EINVAL, "face grids have no-slip walls: bc must be Dirichlet");
+    if (p.kappa || p.coarse_exact)
+      return fail(FAS_EUNSUPPORTED, "face grids: constant kappa and a smoothed coarsest level only");
+  }
 
   fas_ctx* c = new fas_ctx();
   c->p = p;
@@ -1080,14 +1146,8 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
     return bail(fail(FAS_ENOMEM, "fproj"));
   // kernel attributes, set before any launch or stream capture
   cudaError_t e = stream2d_prepare();
-  for (cudaError_t ek : {cudaFuncSetAttribute(k_coarse_smem<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kCoarseSmemLimit),
-                         cudaFuncSetAttribute(k_coarse_smem<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kCoarseSmemLimit),
-                         cudaFuncSetAttribute(k_coarse_smem<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kCoarseSmemLimit),
-                         cudaFuncSetAttribute(k_coarse_smem<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kCoarseSmemLimit)})
+  for (cudaError_t ek : {coarse_attr<double, 2>(), coarse_attr<double, 3>(), coarse_attr<float, 2>(),
+                         coarse_attr<float, 3>()})
     if (e == cudaSuccess) e = ek;
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return bail(fail(FAS_ECUDA, std::string("fas_create: ") + cudaGetErrorString(e)));
@@ -1179,6 +1239,7 @@ fas_status fas_heat_adjoint(fas_ctx* c, const double* u0, const double* fsrc, do
   if (!u0 || !dL_duT || nsteps < 1) return fail(FAS_EINVAL, "fas_heat_adjoint: bad argument");
   if (c->p.alpha != 1.0 || std::fabs(c->p.beta - dt) > 1e-15 * std::fabs(dt))
     return fail(FAS_EINVAL, "fas_heat_adjoint: context must have alpha = 1 and beta = dt");
+  if (c->p.location != FAS_CELL) return fail(FAS_EUNSUPPORTED, "fas_heat_adjoint: cell-centred unknowns only");
   const int64_t n = c->shape[0].cells();
   const size_t bytes = n * sizeof(double);
   const int K = ckpt_every > 0 ? std::min(ckpt_every, nsteps) : nsteps;
@@ -1434,9 +1495,9 @@ fas_status fas_restrict(fas_ctx* c, int level, const double* u, double* uc) {
   {
     Prof pr(c, FAS_K_RESTRICT, level, (double)s.cells());
     if (c->p.dim == 2)
-      k_restrict<double, 2><<<grid_for(c, nc), kBlock, 0, c->stream>>>(uc, nullptr, nullptr, u, nullptr, s.nx, s.ny, s.nz);
+      launch_restrict<double, 2>(c, nc, uc, nullptr, nullptr, u, nullptr, s.nx, s.ny, s.nz);
     else
-      k_restrict<double, 3><<<grid_for(c, nc), kBlock, 0, c->stream>>>(uc, nullptr, nullptr, u, nullptr, s.nx, s.ny, s.nz);
+      launch_restrict<double, 3>(c, nc, uc, nullptr, nullptr, u, nullptr, s.nx, s.ny, s.nz);
   }
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   CUDA_TRY(cudaGetLastError());
@@ -1450,9 +1511,9 @@ fas_status fas_prolong_add(fas_ctx* c, int level, double* u, const double* cc) {
   {
     Prof pr(c, FAS_K_PROLONG, level, (double)s.cells());
     if (c->p.dim == 2)
-      k_prolong<double, 2><<<grid_for(c, nc), kBlock, 0, c->stream>>>(u, cc, nullptr, s.nx, s.ny, s.nz);
+      launch_prolong<double, 2>(c, s.cells(), u, cc, nullptr, s.nx, s.ny, s.nz);
     else
-      k_prolong<double, 3><<<grid_for(c, nc), kBlock, 0, c->stream>>>(u, cc, nullptr, s.nx, s.ny, s.nz);
+      launch_prolong<double, 3>(c, s.cells(), u, cc, nullptr, s.nx, s.ny, s.nz);
   }
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   CUDA_TRY(cudaGetLastError());

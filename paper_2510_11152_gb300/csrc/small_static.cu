@@ -101,9 +101,10 @@ extern "C" fas_status fas_vcycle_small_static(const fas_params* p, double* u, co
   if (!p || !u || !f) return fail_static(FAS_EINVAL, "fas_vcycle_small_static: null argument");
   if (p->dim != 2 && p->dim != 3) return fail_static(FAS_EINVAL, "fas_vcycle_small_static: dim must be 2 or 3");
   if (ncycles < 1) return fail_static(FAS_EINVAL, "fas_vcycle_small_static: ncycles must be >= 1");
-  if (p->kappa || p->coarse_exact || p->precision != FAS_FP64)
+  if (p->kappa || p->coarse_exact || p->precision != FAS_FP64 || p->location != FAS_CELL)
     return fail_static(FAS_EUNSUPPORTED,
-                       "fas_vcycle_small_static: constant kappa, smoothed coarsest level and float64 only");
+                       "fas_vcycle_small_static: cell-centred unknowns, constant kappa, smoothed coarsest level "
+                       "and float64 only");
   for (int a = 0; a < p->dim; ++a)
     if (p->n[a] < 2 || (p->n[a] & (p->n[a] - 1)))
       return fail_static(FAS_EINVAL, "fas_vcycle_small_static: every n must be a power of two >= 2");
@@ -130,6 +131,7 @@ extern "C" fas_status fas_vcycle_small_static(const fas_params* p, double* u, co
     L.lx = log2i(nx);
     L.ly = log2i(ny);
     L.lz = log2i(nz);
+    L.fax = -1;
     const double h2 = h * h;
     L.h2 = h2;
     L.ih2 = 1.0 / h2;
@@ -192,11 +194,11 @@ extern "C" fas_status fas_vcycle_small_static(const fas_params* p, double* u, co
   A.nuc = p->nu_coarse > 0 ? p->nu_coarse : p->nu1;
   for (int k = 0; k < ncycles; ++k) {
     if (dim == 2) {
-      cudaFuncSetAttribute(k_coarse_smem<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStaticSmem);
-      k_coarse_smem<double, 2><<<1, 1024, smem, st>>>(A, S, u, f);
+      cudaFuncSetAttribute(k_coarse_smem<double, 2, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStaticSmem);
+      k_coarse_smem<double, 2, -1><<<1, 1024, smem, st>>>(A, S, u, f);
     } else {
-      cudaFuncSetAttribute(k_coarse_smem<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStaticSmem);
-      k_coarse_smem<double, 3><<<1, 1024, smem, st>>>(A, S, u, f);
+      cudaFuncSetAttribute(k_coarse_smem<double, 3, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStaticSmem);
+      k_coarse_smem<double, 3, -1><<<1, 1024, smem, st>>>(A, S, u, f);
     }
   }
   if (dim == 2)

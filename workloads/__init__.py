@@ -34,6 +34,8 @@ TAG_SIZES = 5
 TAG_COEF = 6
 TAG_NORMAL = 7
 TAG_INIT = 8
+TAG_VEL = 9  # 9, 10, 11: velocity components x, y, z
+TAG_PRES = 12
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -194,3 +196,46 @@ def adjoint_heat(n: int = 1024, nsteps: int = 50):
 def random_field(shape, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
     """Uniform U(lo, hi) field (random initial guesses and random test operands)."""
     return lo + (hi - lo) * uniform(seed, TAG_INIT, int(np.prod(shape))).reshape(shape)
+
+
+# ---------------------------------------------------------------------------------------------
+# staggered (MAC) grid states: component a of the velocity on the faces normal to physical axis a,
+# stored in the cell-field shape with slot s = face s+1 along that axis and the far wall face (always
+# 0) in the last slot
+# ---------------------------------------------------------------------------------------------
+
+NS_NAMES = ("U", "V", "W")
+
+
+def zero_wall_slot(v: np.ndarray, comp: int) -> np.ndarray:
+    """Set the stored far-wall slot of a face field of component comp to 0 (layout only)."""
+    dim = v.ndim
+    sl = [slice(None)] * dim
+    sl[dim - 1 - comp] = v.shape[dim - 1 - comp] - 1
+    v[tuple(sl)] = 0.0
+    return v
+
+
+def ns_state(shape, seed: int, amplitude: float = 0.5) -> dict:
+    """Eight fields of a synthetic flow state: each velocity component a sum of 6 Gaussians (sigma
+    0.15, amplitudes U(-1,1)) times `amplitude`, zero on its wall slot; pressure 0.1 x 4 Gaussians
+    (sigma 0.2); the *_new work fields zero. Flow in every direction, for parity tests."""
+    dim = len(shape)
+    out = {}
+    for a in range(dim):
+        v = amplitude * gaussian_sum(shape, seed, TAG_VEL + a, 6, 0.15)
+        out[NS_NAMES[a] + "_old"] = zero_wall_slot(v, a)
+        out[NS_NAMES[a] + "_new"] = np.zeros(shape)
+    out["P_old"] = 0.1 * gaussian_sum(shape, seed, TAG_PRES, 4, 0.2)
+    out["P_new"] = np.zeros(shape)
+    return out
+
+
+def ns_cavity(n: int = 256, dim: int = 3, nsteps: int = 20):
+    """Lid-driven cavity on [0,1]^dim: n cells per axis, Re 100, dt 1e-3, the top wall of the last
+    axis moving with velocity 1 along x, fluid at rest at t = 0."""
+    shape = (n,) * dim
+    fields = {NS_NAMES[a] + k: np.zeros(shape) for a in range(dim) for k in ("_old", "_new")}
+    fields["P_old"] = np.zeros(shape)
+    fields["P_new"] = np.zeros(shape)
+    return dict(shape=shape, h=1.0 / n, Re=100.0, dt=1e-3, nsteps=nsteps, lid=(1.0, 0.0, 0.0), fields=fields)

@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--inner", type=int, default=0, help="float32 cycles per refinement step (0: tune)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison arm")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the other workloads (3D heat, NS cavity, batched solves, adjoint)")
     return ap.parse_args()
 
 
@@ -342,6 +344,13 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(w)
 
+    secondary = None
+    if not args.no_secondary:
+        del u0_d, f_d, u_d, u_final
+        fas.fas_destroy(ctx)
+        torch.cuda.empty_cache()
+        secondary = secondary_workloads(dev, stream)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -355,11 +364,167 @@ def run_ours(args, ws, rank, local):
             "converged_all": converged, "last_step_info": last[-1].as_dict(),
             "fp64": fp64, "roofline": roof, "xmcgs": xm, "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "secondary": secondary,
         }
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _event_ms(stream, fn, warmup=1):
+    """fn() after `warmup` untimed calls, timed with CUDA events on the solver's stream."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def secondary_workloads(dev, stream):
+    """The other workloads of the method, each once after one warm-up run (float64 vs mixed where both
+    apply): 3D heat 512^3, the 256^3 lid-driven cavity projection steps, 96 batched Helmholtz solves in
+    one graph launch, the 1024^2 adjoint heat run. Inputs are the seeded recipes of workloads/."""
+    import numpy as np
+    import torch
+
+    import paper_2510_11152_gb300 as fas
+    from workloads import (adjoint_heat, batched_helmholtz, batched_problem_rhs, heat3d, ns_cavity)
+
+    out = {}
+    mc = lambda cells, cycles, ms: cells * cycles / (ms / 1e3) / 1e6  # noqa: E731
+
+    # 3D heat, 512^3, Neumann, dt 1e-4, 10 steps
+    w = heat3d()
+    shape, h, dt, nsteps = w["shape"], w["h"], w["dt"], w["nsteps"]
+    cells = int(np.prod(shape))
+    u0 = torch.from_numpy(w["u0"]).to(dev)
+    f = torch.from_numpy(w["fsrc"]).to(dev) if w.get("fsrc") is not None else None
+    u = torch.empty_like(u0)
+    res = {}
+    for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
+        ctx = fas.fas_create(fas.make_params(shape, h, alpha=1.0, beta=dt, coarsest=4, precision=prec), stream=stream)
+
+        def run():
+            u.copy_(u0)
+            return fas.fas_heat_run(ctx, u, f, dt, nsteps)
+        ms, infos = _event_ms(stream, run)
+        cyc = sum(i.cycles for i in infos)
+        res[name] = {"ms_per_run": ms, "vcycles_per_run": cyc, "Mcells_vcycles_per_s": mc(cells, cyc, ms),
+                     "converged_all": all(i.converged for i in infos), "u": u.clone()}
+        fas.fas_destroy(ctx)
+    out["heat3d_512"] = {
+        "workload": "heat3d-512^3-neumann-dt1e-4-10steps-tol1e-10-V(2,2)-coarsest4",
+        "mixed": {k: v for k, v in res["mixed"].items() if k != "u"},
+        "fp64": {k: v for k, v in res["fp64"].items() if k != "u"},
+        "speedup_mixed_vs_fp64_time": res["fp64"]["ms_per_run"] / res["mixed"]["ms_per_run"],
+        "mixed_vs_fp64_rel_maxdiff": float((res["mixed"]["u"] - res["fp64"]["u"]).abs().max().item()
+                                           / res["fp64"]["u"].abs().max().item())}
+    del u0, f, u, res
+    torch.cuda.empty_cache()
+
+    # NS: first-order projection, lid-driven cavity 256^3, Re 100, dt 1e-3, 20 steps from rest
+    w = ns_cavity(n=256, dim=3, nsteps=20)
+    shape, nsteps = w["shape"], w["nsteps"]
+    cells = int(np.prod(shape))
+    zero = torch.zeros(shape, dtype=torch.float64, device=dev)
+    ns_res = {}
+    for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
+        sp = fas.fas_default_params()
+        sp.precision, sp.kmax, sp.coarsest = prec, 40, 4
+        pp = fas.fas_default_params()
+        pp.precision, pp.kmax, pp.coarsest, pp.coarse_exact = prec, 60, 4, 1
+        ns = fas.ns_create(shape, w["h"], w["Re"], w["dt"], lid=w["lid"], solver=sp, pressure=pp, stream=stream)
+        flds = {k: zero.clone() for k in w["fields"]}
+
+        def run():
+            for t in flds.values():
+                t.zero_()
+            tot, div = [0, 0, 0, 0], 0.0
+            for _ in range(nsteps):
+                infos, div = fas.ns_projection_step(ns, flds, want_div=False)
+                for k in range(4):
+                    tot[k] += infos[k].cycles
+            return tot
+        fas.ns_launch_count(ns, reset=True)
+        ms, tot = _event_ms(stream, run)
+        _, dmax = fas.ns_projection_step(ns, flds, want_div=True)
+        ns_res[name] = {"ms_per_step": ms / nsteps, "vcycles_per_step_u_v_w_p": [c / nsteps for c in tot],
+                        "Mcells_vcycles_per_s": mc(cells, sum(tot), ms), "div_max_after": dmax,
+                        "U": flds["U_old"].clone()}
+        del flds
+        fas.ns_destroy(ns)
+    out["ns_cavity_256"] = {
+        "workload": "ns-first-order-projection-lid-cavity-256^3-Re100-dt1e-3-20steps-WENO3-tol1e-10",
+        "mixed": {k: v for k, v in ns_res["mixed"].items() if k != "U"},
+        "fp64": {k: v for k, v in ns_res["fp64"].items() if k != "U"},
+        "speedup_mixed_vs_fp64_time": ns_res["fp64"]["ms_per_step"] / ns_res["mixed"]["ms_per_step"],
+        "mixed_vs_fp64_rel_maxdiff_U": float((ns_res["mixed"]["U"] - ns_res["fp64"]["U"]).abs().max().item()
+                                             / ns_res["fp64"]["U"].abs().max().item()),
+        "resident_fields": 8}
+    del zero, ns_res
+    torch.cuda.empty_cache()
+
+    # batched: 96 independent 2D Helmholtz problems in one graph launch, mixed precision
+    probs = batched_helmholtz()
+    fs = [torch.from_numpy(batched_problem_rhs(p)).to(dev) for p in probs]
+    ctxs = [fas.fas_create(fas.make_params((p["n"], p["n"]), 1.0 / p["n"], alpha=1.0, beta=p["dt"],
+                                           kappa_const=p["kappa"], coarsest=4, precision=fas.FAS_MIXED),
+                           stream=stream) for p in probs]
+    us = [torch.zeros_like(t) for t in fs]
+
+    def run_b():
+        for t in us:
+            t.zero_()
+        return fas.fas_solve_batched(ctxs, us, fs, stream=stream)
+    ms, infos = _event_ms(stream, run_b)
+    work = sum(p["n"] * p["n"] * i.cycles for p, i in zip(probs, infos))
+    out["batched_96"] = {"workload": "96 2D Helmholtz problems, n in 64..2048, kappa U(0.5,2), dt {1e-4,1e-3}, "
+                                     "mixed, tol 1e-10, one graph launch",
+                         "ms": ms, "Mcells_vcycles_per_s": work / (ms / 1e3) / 1e6,
+                         "fine_cells": sum(p["n"] * p["n"] for p in probs),
+                         "converged_all": all(i.converged for i in infos)}
+    for c in ctxs:
+        fas.fas_destroy(c)
+    del fs, us, ctxs
+    torch.cuda.empty_cache()
+
+    # adjoint: 1024^2 heat with varying kappa, 50 steps, checkpoints every 10
+    w = adjoint_heat()
+    shape = w["shape"]
+    kap = torch.from_numpy(w["kappa"]).to(dev)
+    u0 = torch.from_numpy(w["u0"]).to(dev)
+    fsrc = torch.from_numpy(w["fsrc"]).to(dev)
+    tgt = torch.from_numpy(w["target"]).to(dev)
+    adj = {}
+    for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
+        ctx = fas.fas_create(fas.make_params(shape, w["h"], alpha=1.0, beta=w["dt"], coarsest=4, precision=prec),
+                             stream=stream, kappa=kap)
+        uT = torch.empty_like(u0)
+        g = [torch.empty_like(u0) for _ in range(3)]
+        fwd = torch.empty_like(u0)
+
+        def run_a():
+            fwd.copy_(u0)
+            fas.fas_heat_run(ctx, fwd, fsrc, w["dt"], w["nsteps"])
+            dl = 2.0 * (fwd - tgt)
+            fas.fas_heat_adjoint(ctx, u0, fsrc, w["dt"], w["nsteps"], dl, uT, g[0], g[1], g[2], 10)
+        ms, _ = _event_ms(stream, run_a)
+        adj[name] = {"ms_forward_plus_adjoint": ms, "g_kappa": g[2].clone()}
+        fas.fas_destroy(ctx)
+    out["adjoint_1024"] = {"workload": "adjoint heat 1024^2, varying kappa, 50 steps, checkpoints every 10",
+                           "mixed": {"ms_forward_plus_adjoint": adj["mixed"]["ms_forward_plus_adjoint"]},
+                           "fp64": {"ms_forward_plus_adjoint": adj["fp64"]["ms_forward_plus_adjoint"]},
+                           "mixed_vs_fp64_rel_maxdiff_g_kappa": float(
+                               (adj["mixed"]["g_kappa"] - adj["fp64"]["g_kappa"]).abs().max().item()
+                               / adj["fp64"]["g_kappa"].abs().max().item())}
+    return out
 
 
 def cpu_baseline(w, n_cycles=1):

@@ -179,6 +179,15 @@ fas_status fas_autotune(fas_ctx* ctx, double* u_scratch, const double* f, fas_tu
 fas_status fas_residual(fas_ctx* ctx, int level, const double* u, const double* f, double* out,
                         double* norm2);
 
+/* The refinement residual of the mixed-precision solve on level 0, as the solve computes it:
+ * r32 = (float)(f - A u) rounded to nearest even, norm2 (may be NULL) = ||r32||_2. With a constant
+ * kappa the point equation is evaluated as fma(c, S, fma(-alpha, u, f)), c = beta kappa / h^2, where
+ * S = sum_nb u_nb - M u (M the diagonal's neighbour count plus boundary multiplicities) is summed
+ * exactly in integer arithmetic on the significands and rounded once; cells whose stencil holds a
+ * zero, a subnormal or non-finite value, or values more than 2^5 apart in exponent, use the float64
+ * expression of fas_residual. u, f DEVICE float64, r32 DEVICE float32, nx*ny(*nz) each. */
+fas_status fas_residual_ir(fas_ctx* ctx, const double* u, const double* f, float* r32, double* norm2);
+
 /* `sweeps` X-MCGS sweeps in place on u of level `level` (Sec. 2.3 / Appendix B). */
 fas_status fas_smooth(fas_ctx* ctx, int level, double* u, const double* f, int sweeps);
 
@@ -247,6 +256,14 @@ fas_status fas_prof_read(fas_ctx* ctx, fas_prof_record* out, int cap, int* count
  * caller must serialise them (one stream, or events). */
 fas_status fas_vcycle_small_static(const fas_params* p, double* u, const double* f, int ncycles,
                                    double* res_host, void* stream);
+
+/* Self-test of the integer-arithmetic float32 <-> float64 conversions that the float64 kernels use
+ * instead of the hardware conversions (no counterpart in the paper): converts a fixed list of special
+ * values and, for each of `count` seeded pseudo-random draws, a raw 64-bit pattern, three doubles in
+ * and around float32's exponent range (random, exact-tie and tie +- 1 significands) and two floats,
+ * and compares each result with the hardware conversion. *mismatches (HOST) receives the number of
+ * results that differ in any bit (two NaNs count as equal). Runs on the current device and stream 0. */
+fas_status fas_selftest_conversions(long long count, unsigned long long seed, long long* mismatches);
 
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char* fas_last_error(void);

@@ -107,6 +107,8 @@ def load(path: str | None = None):
         "fas_autotune": (_I, [_P, _P, _P, ctypes.POINTER(fas_tune_result)]),
         "fas_heat_adjoint": (_I, [_P, _P, _P, _D, _I, _P, _P, _P, _P, _P, _I]),
         "fas_prof_read": (_I, [_P, ctypes.c_void_p, _I, ctypes.POINTER(_I)]),
+        "fas_residual_ir": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D)]),
+        "fas_selftest_conversions": (_I, [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]),
         "ns_create": (_I, [_I, ctypes.POINTER(_I), _D, _D, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(fas_params),
                            ctypes.POINTER(fas_params), _P, ctypes.POINTER(_P)]),
         "ns_projection_step": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(fas_info), ctypes.POINTER(_D)]),
@@ -249,6 +251,26 @@ def fas_residual(ctx: _Ctx, level: int, u, f, out=None) -> float:
     _check(load().fas_residual(ctx.handle, level, _dev(u, "u", n), _dev(f, "f", n), _dev(out, "out", n),
                                ctypes.byref(norm)), "fas_residual")
     return norm.value
+
+
+def fas_residual_ir(ctx: _Ctx, u, f, r32) -> float:
+    """The mixed solve's refinement residual r32 = (float)(f - A u) on level 0 (float32 CUDA tensor)."""
+    import torch
+    n = ctx.cells
+    if not isinstance(r32, torch.Tensor) or r32.dtype != torch.float32 or not r32.is_cuda or r32.numel() != n \
+            or not r32.is_contiguous():
+        raise TypeError("r32 must be a contiguous float32 CUDA tensor of %d elements" % n)
+    nrm = _D(0.0)
+    _check(load().fas_residual_ir(ctx.handle, _dev(u, "u", n), _dev(f, "f", n), r32.data_ptr(), ctypes.byref(nrm)),
+           "fas_residual_ir")
+    return nrm.value
+
+
+def fas_selftest_conversions(count: int, seed: int = 1) -> int:
+    """Mismatches between the integer float32<->float64 conversions and the hardware ones."""
+    out = ctypes.c_longlong(0)
+    _check(load().fas_selftest_conversions(int(count), int(seed), ctypes.byref(out)), "fas_selftest_conversions")
+    return out.value
 
 
 def fas_smooth(ctx: _Ctx, level: int, u, f, sweeps: int) -> None:

@@ -6,6 +6,7 @@
 // No pointer here is declared __restrict__ or read through the non-coherent path: the single-CTA
 // kernel writes a level in one step and reads it in the next, separated only by __syncthreads.
 #pragma once
+#include "bits64.cuh"
 #include "common.cuh"
 
 namespace fasmg {
@@ -330,7 +331,7 @@ static __global__ void k_heat_rhs(double* b, const double* u, const double* fsrc
   for (int64_t i = gtid(); i < n; i += gstride()) {
     const double v = fsrc ? fma(dt, fsrc[i], u[i]) : u[i];
     b[i] = v;
-    const float vf = (float)v;
+    const float vf = f64_to_f32_rn_bits(v);
     acc = fmaf(vf, vf, acc);
   }
   const double s = block_sum((double)acc);
@@ -339,9 +340,34 @@ static __global__ void k_heat_rhs(double* b, const double* u, const double* fsrc
 
 // ---- mixed precision (iterative refinement): u += e, and r32 = (float)(b - A u) with its norm
 static __global__ void k_ir_update(double* u, const float* e, int64_t n) {
-  for (int64_t i = gtid(); i < n; i += gstride()) u[i] += (double)e[i];
+  for (int64_t i = gtid(); i < n; i += gstride()) u[i] += f32_to_f64_bits(e[i]);
 }
 
+// Bit patterns of the neighbours of cell (i, j, l) in the order x-, x+, y-, y+, z-, z+ (0 where a
+// neighbour is missing) and the mask of the present ones.
+template <int DIM>
+__device__ __forceinline__ unsigned nb_bits(const double* __restrict__ u, int64_t idx, int i, int j, int l,
+                                            const LevelDesc<double>& L, uint64_t (&nb)[2 * DIM]) {
+  const unsigned long long* ub = reinterpret_cast<const unsigned long long*>(u);
+  const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny;
+  const bool p0 = i > 0, p1 = i < L.nx - 1, p2 = j > 0, p3 = j < L.ny - 1;
+  nb[0] = p0 ? ub[idx - 1] : 0ull;
+  nb[1] = p1 ? ub[idx + 1] : 0ull;
+  nb[2] = p2 ? ub[idx - sy] : 0ull;
+  nb[3] = p3 ? ub[idx + sy] : 0ull;
+  unsigned mask = (unsigned)p0 | ((unsigned)p1 << 1) | ((unsigned)p2 << 2) | ((unsigned)p3 << 3);
+  if constexpr (DIM == 3) {
+    const bool p4 = l > 0, p5 = l < L.nz - 1;
+    nb[4] = p4 ? ub[idx - sz] : 0ull;
+    nb[5] = p5 ? ub[idx + sz] : 0ull;
+    mask |= ((unsigned)p4 << 4) | ((unsigned)p5 << 5);
+  }
+  return mask;
+}
+
+// r32 = (float)(b - A u) and the per-block partial of sum (nscale r32)^2. With constant kappa the
+// point equation is evaluated as fma(c, S, fma(-alpha, u, b)) with S = sum_nb u_nb - M u exact
+// (bits64.cuh); cells where that does not apply take the float64 point equation.
 template <int DIM>
 __global__ void k_ir_residual(float* r32, const double* u, const double* b, LevelDesc<double> L, const float* nsp,
                               double* partials) {
@@ -352,7 +378,23 @@ __global__ void k_ir_residual(float* r32, const double* u, const double* b, Leve
     const int i = (int)(idx & (L.nx - 1));
     const int j = (int)((idx >> L.lx) & (L.ny - 1));
     const int l = (int)(idx >> (L.lx + L.ly));
-    const float rv = (L.fax >= 0 && frozen(L, i, j, l)) ? 0.f : (float)residual_point<double, DIM>(u, b, L, idx, i, j, l);
+    float rv = 0.f;
+    if (!(L.fax >= 0 && frozen(L, i, j, l))) {
+      double r = 0.0, S = 0.0;
+      bool done = false;
+      if (!L.varkappa) {
+        uint64_t nb[2 * DIM];
+        const unsigned mask = nb_bits<DIM>(u, idx, i, j, l, L, nb);
+        const double uc = u[idx];
+        const int cls = bclass<DIM>(i, j, l, L.nx, L.ny, L.nz);
+        if (stencil_diff_exact<2 * DIM>((uint64_t)__double_as_longlong(uc), nb, mask, L.mt[cls], &S)) {
+          r = fma(L.c, S, fma(-L.alpha, uc, b[idx]));
+          done = true;
+        }
+      }
+      if (!done) r = residual_point<double, DIM>(u, b, L, idx, i, j, l);
+      rv = f64_to_f32_rn_bits(r);
+    }
     r32[idx] = rv;
     const float rs = rv * nscale;
     acc = fmaf(rs, rs, acc);

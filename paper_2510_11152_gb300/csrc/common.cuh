@@ -38,7 +38,9 @@ struct LevelDesc {
   const T* wz;     // same along z (0 at l = nz-1)
   const T* rD;     // 1 / D
   const T* Dh;     // D / h^2
+  T alpha;         // alpha of A u = alpha u - beta div(kappa grad u)
   T a[kClasses], b[kClasses], d[kClasses];
+  unsigned char mt[kClasses];  // M of d = alpha + c M: neighbours plus boundary multiplicities
 };
 
 // boundary class: bit 0 x_lo, 1 x_hi, 2 y_lo, 3 y_hi, 4 z_lo, 5 z_hi

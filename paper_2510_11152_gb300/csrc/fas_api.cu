@@ -17,6 +17,7 @@
 
 #include "basic_kernels.cuh"
 #include "context.h"
+#include "ir_strip.h"
 #include "stream2d.h"
 
 using namespace fasmg;
@@ -121,6 +122,7 @@ LevelDesc<T> make_desc(const fas_params& p, const LevelShape& s) {
   L.ih2 = (T)(1.0 / h2);
   const double bk = p.beta * p.kappa_const;
   L.c = (T)(bk / h2);
+  L.alpha = (T)p.alpha;
   const int nfaces = 2 * p.dim;
   for (int cls = 0; cls < kClasses; ++cls) {
     double m = 0.0;
@@ -132,6 +134,7 @@ LevelDesc<T> make_desc(const fas_params& p, const LevelShape& s) {
       m += boundary ? mb : 1.0;
     }
     const double D = p.alpha * h2 + bk * m;
+    L.mt[cls] = (unsigned char)m;
     L.a[cls] = (T)(D != 0.0 ? bk / D : 0.0);
     L.b[cls] = (T)(D != 0.0 ? h2 / D : 0.0);
     L.d[cls] = (T)(D / h2);
@@ -610,17 +613,25 @@ void enqueue_norm(fas_ctx* c, const double* x, const float* nsp, double* out) {
 }
 
 // ||b - A u||_2 into *out; mixed precision also leaves r32 = (float)(b - A u) in h32.f[0]
+// r32 = (float)(b - A u) on level 0 with per-block partials of its (nsp-scaled) squares; returns the
+// number of partials.
+int launch_ir_residual(fas_ctx* c, float* r32, const double* u, const double* b, const float* nsp) {
+  const LevelDesc<double>& L = c->h64.desc[0];
+  const int64_t n = c->shape[0].cells();
+  int g = grid_for(c, n);
+  Prof pr(c, FAS_K_IR, 0, (double)n);
+  if (c->p.dim == 2 && ir_strip_supported(L))
+    launch_ir_strip(r32, u, b, L, nsp, c->partials, c->sm_count, c->max_blocks, &g, c->stream);
+  else if (c->p.dim == 2)
+    k_ir_residual<2><<<g, kBlock, 0, c->stream>>>(r32, u, b, L, nsp, c->partials);
+  else
+    k_ir_residual<3><<<g, kBlock, 0, c->stream>>>(r32, u, b, L, nsp, c->partials);
+  return g;
+}
+
 void enqueue_residual_norm(fas_ctx* c, const double* u, const double* b, const float* nsp, double* out) {
   if (c->p.precision == FAS_MIXED) {
-    const int64_t n = c->shape[0].cells();
-    const int g = grid_for(c, n);
-    {
-      Prof pr(c, FAS_K_IR, 0, (double)n);
-      if (c->p.dim == 2)
-        k_ir_residual<2><<<g, kBlock, 0, c->stream>>>(c->h32.f[0], u, b, c->h64.desc[0], nsp, c->partials);
-      else
-        k_ir_residual<3><<<g, kBlock, 0, c->stream>>>(c->h32.f[0], u, b, c->h64.desc[0], nsp, c->partials);
-    }
+    const int g = launch_ir_residual(c, c->h32.f[0], u, b, nsp);
     Prof pr(c, FAS_K_NORM, 0, 0.0);
     k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, out, nsp);
   } else if (c->p.dim == 2) {
@@ -1041,6 +1052,69 @@ cudaError_t coarse_attr() {
                                               (int)kCoarseSmemLimit)})
     if (e == cudaSuccess) e = ek;
   return e;
+}
+
+// Pseudo-random 64-bit patterns for the conversion self-test (SplitMix64 in counter mode).
+__device__ __forceinline__ uint64_t st_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ bool same_or_both_nan_f(float a, float b) {
+  return __float_as_uint(a) == __float_as_uint(b) || (a != a && b != b);
+}
+
+__device__ __forceinline__ bool same_or_both_nan_d(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b) || (a != a && b != b);
+}
+
+// For each k: a raw 64-bit pattern, a double in and around float32's exponent range (random, exact
+// tie and tie +- 1 significands), and the low 32 bits as a float; both conversions of each checked
+// against the hardware ones.
+static __global__ void k_selftest_conv(long long count, unsigned long long seed, unsigned long long* bad) {
+  unsigned long long nbad = 0;
+  for (long long k = gtid(); k < count; k += gstride()) {
+    const uint64_t z = st_mix(seed + 0x9E3779B97F4A7C15ull * (uint64_t)(k + 1));
+    const uint64_t z2 = st_mix(z ^ 0xD1B54A32D192ED03ull);
+    uint64_t pats[4];
+    pats[0] = z;
+    const uint64_t E = 896 - 40 + (z2 % 300);  // float32 subnormals up to overflow
+    const uint64_t sign = z2 & (1ull << 63);
+    const uint64_t hiM = z & (((1ull << 23) - 1) << 29);
+    pats[1] = sign | (E << 52) | (z & kMant52);
+    pats[2] = sign | (E << 52) | hiM | (1ull << 28);                     // exact tie at float precision
+    pats[3] = sign | (E << 52) | hiM | ((1ull << 28) + ((z2 >> 8) & 1 ? 1 : -1));
+    for (int q = 0; q < 4; ++q) {
+      const double d = __longlong_as_double((long long)pats[q]);
+      if (!same_or_both_nan_f(f64_to_f32_rn_bits(d), __double2float_rn(d))) ++nbad;
+    }
+    const float fx = __uint_as_float((uint32_t)z);
+    const float fy = __uint_as_float((uint32_t)(z2 >> 32) & 0x807FFFFFu);  // float32 subnormals
+    if (!same_or_both_nan_d(f32_to_f64_bits(fx), (double)fx)) ++nbad;
+    if (!same_or_both_nan_d(f32_to_f64_bits(fy), (double)fy)) ++nbad;
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+static __global__ void k_selftest_specials(unsigned long long* bad) {
+  const uint64_t dpat[] = {0ull, 1ull << 63, 0x7FF0000000000000ull, 0xFFF0000000000000ull, 0x7FF8000000000000ull,
+                           0x47EFFFFFE0000000ull, 0x47EFFFFFF0000000ull, 0x47EFFFFFEFFFFFFFull,
+                           0x3690000000000000ull, 0x3680000000000000ull, 0x3680000000000001ull,
+                           0x36A0000000000000ull, 0x380FFFFFF0000000ull, 0x0000000000000001ull,
+                           0x3FF0000000000000ull, 0xBFF0000010000000ull};
+  const uint32_t fpat[] = {0u, 0x80000000u, 0x7F800000u, 0xFF800000u, 0x7FC00000u, 0x00000001u, 0x007FFFFFu,
+                           0x00800000u, 0x7F7FFFFFu, 0x3F800000u, 0x80000001u, 0x00400000u};
+  unsigned long long nbad = 0;
+  for (uint64_t p : dpat) {
+    const double d = __longlong_as_double((long long)p);
+    if (!same_or_both_nan_f(f64_to_f32_rn_bits(d), __double2float_rn(d))) ++nbad;
+  }
+  for (uint32_t p : fpat) {
+    const float f = __uint_as_float(p);
+    if (!same_or_both_nan_d(f32_to_f64_bits(f), (double)f)) ++nbad;
+  }
+  *bad += nbad;
 }
 
 extern "C" {
@@ -1472,6 +1546,38 @@ fas_status fas_residual(fas_ctx* c, int level, const double* u, const double* f,
   double v = 0.0;
   STATUS_TRY(sync_read(c, &v));
   if (norm2) *norm2 = v;
+  return FAS_OK;
+}
+
+fas_status fas_residual_ir(fas_ctx* c, const double* u, const double* f, float* r32, double* norm2) {
+  STATUS_TRY(check_ctx(c));
+  if (!u || !f || !r32) return fail(FAS_EINVAL, "fas_residual_ir: null field");
+  const int g = launch_ir_residual(c, r32, u, f, nullptr);
+  {
+    Prof pr(c, FAS_K_NORM, 0, 0.0);
+    k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, nullptr);
+  }
+  double v = 0.0;
+  STATUS_TRY(sync_read(c, &v));
+  if (norm2) *norm2 = v;
+  return FAS_OK;
+}
+
+fas_status fas_selftest_conversions(long long count, unsigned long long seed, long long* mismatches) {
+  if (count < 0 || !mismatches) return fail(FAS_EINVAL, "fas_selftest_conversions: bad argument");
+  unsigned long long* d = nullptr;
+  CUDA_TRY(cudaMalloc(&d, sizeof(unsigned long long)));
+  cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    k_selftest_specials<<<1, 1>>>(d);
+    if (count > 0) k_selftest_conv<<<1024, 256>>>(count, seed, d);
+    e = cudaGetLastError();
+  }
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(FAS_ECUDA, std::string("fas_selftest_conversions: ") + cudaGetErrorString(e));
+  *mismatches = (long long)h;
   return FAS_OK;
 }
 

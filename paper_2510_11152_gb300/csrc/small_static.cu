@@ -136,11 +136,13 @@ extern "C" fas_status fas_vcycle_small_static(const fas_params* p, double* u, co
     L.h2 = h2;
     L.ih2 = 1.0 / h2;
     L.c = bk / h2;
+    L.alpha = p->alpha;
     for (int cls = 0; cls < kClasses; ++cls) {
       double m = 0.0;
       for (int face = 0; face < nfaces; ++face)
         m += ((cls >> face) & 1) ? (p->bc[face] == FAS_BC_DIRICHLET ? 2.0 : 0.0) : 1.0;
       const double D = p->alpha * h2 + bk * m;
+      L.mt[cls] = (unsigned char)m;
       L.a[cls] = D != 0.0 ? bk / D : 0.0;
       L.b[cls] = D != 0.0 ? h2 / D : 0.0;
       L.d[cls] = D / h2;

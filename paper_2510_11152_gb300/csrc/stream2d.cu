@@ -26,6 +26,7 @@
 // float32 kernels.
 #include <mutex>
 
+#include "bits64.cuh"
 #include "common.cuh"
 #include "stream2d.h"
 
@@ -413,10 +414,10 @@ __device__ __forceinline__ void post_body(Ring<UPD>& R, const StripGeo& g, int y
         const float4 e = U[(it - LW) & M];
         if (UPD) {  // mixed precision: u64 += e, the float64 update of the refinement step
           double2* dst = reinterpret_cast<double2*>(u64 + (int64_t)yw * nx + g.xl);
-          ua.x += (double)e.x;
-          ua.y += (double)e.y;
-          ub.x += (double)e.z;
-          ub.y += (double)e.w;
+          ua.x += f32_to_f64_bits(e.x);
+          ua.y += f32_to_f64_bits(e.y);
+          ub.x += f32_to_f64_bits(e.z);
+          ub.y += f32_to_f64_bits(e.w);
           dst[0] = ua;
           dst[1] = ub;
         } else {

@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--inner", type=int, default=0, help="float32 cycles per refinement step (0: tune)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison arm")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every kernel from the host instead of one CUDA graph per solve (the same "
+                         "kernels; ncu cannot list kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the other workloads (3D heat, NS cavity, batched solves, adjoint)")
     return ap.parse_args()
@@ -141,13 +144,12 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------------------------
-# algorithmic work per cell of each kernel family (bytes or float64 operations); see the design doc
+# algorithmic work per cell of each kernel family (bytes or float64 operations)
 # ---------------------------------------------------------------------------------------------
 
 def kernel_work(family, level, inner_first_zero=True):
     """(bound, per-cell work, unit) of a kernel family on a level of the mixed-precision solver.
-    float32 fused kernels: bytes that must cross HBM once (b = 4); float64 refinement kernels: FP64
-    FLOPs (DFMA counted as 2) for the residual, bytes for the update."""
+    Bytes that must cross HBM once (b = 4 for float32 fields, 8 for float64)."""
     b = 4.0
     if family == "smooth":  # fused pre-smoothing: f (+u, +R(r)) in, u and R(u), R(r) out
         if level == 0:
@@ -155,8 +157,8 @@ def kernel_work(family, level, inner_first_zero=True):
         return "hbm", 4.5 * b, "B"
     if family == "prolong":  # fused post-smoothing: u, f, u_c in; u out
         return "hbm", 3.25 * b, "B"
-    if family == "ir":  # r = b - A u: 3 DADD + 2 DFMA per cell
-        return "alu", 7.0, "FLOP"
+    if family == "ir":  # r32 = (float)(b - A u): u, b in (float64), r32 out; the exact-difference kernel
+        return "hbm", 8.0 + 8.0 + b, "B"  # also has a float64 floor of 2 DFMA per cell, about equal
     if family == "update":  # fused post-smoothing + u += e: u, f, u_c in (float32), float64 u in/out
         return "hbm", 3.0 * b + 1.0 + 16.0, "B"
     return None, None, None
@@ -200,7 +202,8 @@ def run_ours(args, ws, rank, local):
 
     def make(precision, inner=1):
         return fas.fas_create(fas.make_params(shape, h, alpha=1.0, beta=dt, coarsest=4, precision=precision,
-                                              inner_cycles=inner), stream=stream)
+                                              inner_cycles=inner, use_graph=0 if args.no_graph else 1),
+                              stream=stream)
 
     def one_run(ctx, inner):
         u_d.copy_(u0_d)
@@ -360,7 +363,8 @@ def run_ours(args, ws, rank, local):
                        "grid": [n, n], "time_steps_per_run": nsteps, "precision": "mixed",
                        "inner_float32_cycles": inner, "vcycles_per_run": cycles / args.steps,
                        "l2": "inputs larger than L2 (512 MiB per float64 field)",
-                       "parallelism": "replicas" if ws > 1 else "single-gpu"},
+                       "parallelism": "replicas" if ws > 1 else "single-gpu",
+                       "launch": "host loop" if args.no_graph else "one CUDA graph per solve"},
             "converged_all": converged, "last_step_info": last[-1].as_dict(),
             "fp64": fp64, "roofline": roof, "xmcgs": xm, "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,

@@ -240,7 +240,7 @@ fas_status fas_prof_read(fas_ctx* ctx, fas_prof_record* out, int cap, int* count
  * fas_vcycle_small_static runs ncycles V-cycles (the V-cycle of fas_vcycle, float64, constant kappa,
  * coarsest level smoothed) on device field u in place, for right-hand side f, with no context and no
  * allocation: the whole level hierarchy is held in one CTA's shared memory, and the only global
- * scratch -- the level descriptors and the residual-norm slot, about 26 KB -- is a static device
+ * scratch -- the level descriptors and the residual-norm slot, about 27 KB -- is a static device
  * array that every GPU loading the library keeps until the process exits.
  *   p         problem and smoothing parameters as for fas_create (kappa must be NULL, coarse_exact 0,
  *             precision FAS_FP64; kmax, tol, inner_cycles, use_graph, path, seg_rows are ignored)

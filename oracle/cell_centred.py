@@ -13,7 +13,7 @@ Follows the paper section by section:
                                       3D analogues with eight children)
   * heat stepping ................... Sec. 1 (backward Euler, new step overwrites the old)
 
-Readings where the paper is silent, garbled or self-contradictory (each is listed in the design doc):
+Readings where the paper is silent, garbled or self-contradictory:
   G1  Boundary ghosts: homogeneous Dirichlet is ghost = -adjacent cell (Eq. boundry1, first half);
       homogeneous Neumann is ghost = adjacent cell (Eq. boundry1, second half). Each face of the
       box carries one of the two kinds, chosen by the caller.

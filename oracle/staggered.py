@@ -15,7 +15,7 @@ cell-field shape; along its own axis, slot s holds face s+1 (faces 1..n-1 are th
 n-1 holds the far wall face n, whose normal velocity is 0 and is never changed; face 0 (the near wall)
 is not stored and is 0.
 
-Readings (listed in DESIGN.md):
+Readings:
   G9  Appendix D's restriction is printed with the roles of i and j transposed. Read: weights
       (1, 2, 1)/4 across the three fine faces 2i-1/2, 2i+1/2, 2i+3/2 of the normal direction times
       (1, 1)/2 over the two fine cells of each tangential direction. Prolongation as printed: a fine

@@ -38,7 +38,7 @@ struct StaticScratch {
   double norm[2];
 };
 
-// The scratch: about 26 KB.
+// The scratch: about 27 KB.
 static __device__ __align__(256) StaticScratch g_static_scratch;
 
 namespace {

@@ -48,15 +48,18 @@ fas_status ns_create(int dim, const int n[3], double h, double Re, double dt, in
                      const fas_params* solver, const fas_params* pressure, void* stream, ns_ctx** out);
 
 /* One time step of the first-order projection scheme (Sec. 4.2):
- *   f_c = c^n - dt (u^n . grad) c^n - dt (grad p^n)_c        (third-order WENO convection)
+ *   f_c = c^n - dt (u^n . grad) c^n - dt (grad p^n)_c + dt F_c   (third-order WENO convection)
  *   (I - dt/Re Lap) c~ = f_c        from the initial guess c^n, into C_new, for every component
  *   -dt Lap p~ = -div u~            homogeneous Neumann, mean 0, into P_new (zero initial guess)
  *   c^{n+1} = c~ - dt (grad p~)_c   into C_old;   p^{n+1} = p^n + p~ into P_old.
+ * force (may be NULL, as may each entry): DEVICE pointers to the body force F_c of each component at
+ * t^{n+1} on its faces (the face-field layout above), e.g. the source of a manufactured solution.
  * info (may be NULL) receives 4 reports: the solves of U, V, W (zeroed in 2D) and of the pressure.
  * div_max (HOST pointer, may be NULL) receives max |div u^{n+1}| over the cells.
  * A solve that stops at kmax without reaching its tolerance does not stop the step: the step is
  * completed and FAS_ENOTCONV returned. Non-finite residuals return FAS_ENONFINITE at once. */
-fas_status ns_projection_step(ns_ctx* ns, double* const fields[8], fas_info info[4], double* div_max);
+fas_status ns_projection_step(ns_ctx* ns, double* const fields[8], const double* const force[3], fas_info info[4],
+                              double* div_max);
 
 /* Kernel launches issued by the context and its solvers since creation or the last reset. */
 long long ns_launch_count(ns_ctx* ns, int reset);

@@ -426,13 +426,15 @@ class NSParams:
     pressure: cc.Params = None
 
 
-def projection_step(fields: dict, shape, h, prm: NSParams):
+def projection_step(fields: dict, shape, h, prm: NSParams, force=None):
     """Scheme first-1..4 in the order of the 8-field memory-efficient table:
         f_c = c^n - dt (u^n . grad c^n)_WENO3 - dt (grad p^n)_c          (source, into a solver temporary)
         (I - dt/Re Lap) tilde-c = f_c, from c^n, into C_new              (viscous solves)
         dt Lap tilde-p = div tilde-u, i.e. -dt Lap tilde-p = -div tilde-u (pressure, Neumann, mean 0) into P_new
         c^{n+1} = tilde-c - dt (grad tilde-p)_c into C_old; p^{n+1} = p^n + tilde-p into P_old.
     fields: U_new, U_old, V_new, V_old, [W_new, W_old,] P_new, P_old (numpy arrays, updated in place).
+    force (optional): per component, the body force at t^{n+1} on its faces; it enters the viscous
+    right-hand side as + dt F (backward Euler on the forced momentum equation).
     Returns the solve infos and max |div u^{n+1}|."""
     dim = len(shape)
     names = ["U", "V", "W"][:dim]
@@ -445,6 +447,8 @@ def projection_step(fields: dict, shape, h, prm: NSParams):
     infos = []
     for comp, nm in enumerate(names):
         f = vel_n[comp] - dt * convection(vel_n, comp, h, prm.lid) - dt * pressure_gradient(p_n, comp, h)
+        if force is not None and force[comp] is not None:
+            f = f + dt * np.asarray(force[comp], dtype=np.float64)
         op = FaceOperator(shape, h, 1.0, beta, comp)
         f = f + lid_rhs(shape, comp, beta, h, prm.lid)
         f[frozen_slice(op)] = 0.0

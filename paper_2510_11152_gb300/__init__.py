@@ -111,7 +111,8 @@ def load(path: str | None = None):
         "fas_selftest_conversions": (_I, [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]),
         "ns_create": (_I, [_I, ctypes.POINTER(_I), _D, _D, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(fas_params),
                            ctypes.POINTER(fas_params), _P, ctypes.POINTER(_P)]),
-        "ns_projection_step": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(fas_info), ctypes.POINTER(_D)]),
+        "ns_projection_step": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(fas_info),
+                                    ctypes.POINTER(_D)]),
         "ns_launch_count": (ctypes.c_longlong, [_P, _I]),
         "ns_destroy": (_I, [_P]),
     }
@@ -374,14 +375,19 @@ def ns_create(shape, h: float, Re: float, dt: float, lid=(1.0, 0.0, 0.0), order:
     return _NsCtx(out, shape)
 
 
-def ns_projection_step(ns: _NsCtx, fields: dict, want_div: bool = True, allow_notconv: bool = False):
+def ns_projection_step(ns: _NsCtx, fields: dict, want_div: bool = True, allow_notconv: bool = False, force=None):
     """One projection step on the eight resident fields (dict of float64 CUDA tensors named as in
-    NS_FIELDS; W_* absent in 2D). Returns (infos[4], max |div u^{n+1}| or None)."""
+    NS_FIELDS; W_* absent in 2D); force: optional list of per-component body-force tensors at t^{n+1}.
+    Returns (infos[4], max |div u^{n+1}| or None)."""
     n = ns.cells
     ptrs = (_P * 8)(*[_dev(fields.get(k), k, n) for k in NS_FIELDS])
+    fptr = None
+    if force is not None:
+        fl = list(force) + [None] * (3 - len(force))
+        fptr = (_P * 3)(*[_dev(t, "force", n) for t in fl[:3]])
     infos = (fas_info * 4)()
     dmax = _D(0.0)
-    st = load().ns_projection_step(ns.handle, ptrs, infos, ctypes.byref(dmax) if want_div else None)
+    st = load().ns_projection_step(ns.handle, ptrs, fptr, infos, ctypes.byref(dmax) if want_div else None)
     if not (allow_notconv and st == FAS_ENOTCONV):
         _check(st, "ns_projection_step")
     return [infos[k] for k in range(4)], (dmax.value if want_div else None)

@@ -94,13 +94,14 @@ __device__ __forceinline__ double weno3(double a, double b, double c) {
   return (a0 * p0 + a1 * p1) / (a0 + a1);
 }
 
-// f_C = c^n - dt (u^n . grad c^n)_WENO3 - dt (p^n_{s+1} - p^n_s)/h, plus the lid's tangential wall
-// velocity folded into the cells next to the top wall (2 beta g / h^2, the ghost 2g - inside of the
-// viscous operator), 0 on the wall slot. C is the component (= its index axis).
+// f_C = c^n - dt (u^n . grad c^n)_WENO3 - dt (p^n_{s+1} - p^n_s)/h + dt F (F: body force at t^{n+1},
+// optional), plus the lid's tangential wall velocity folded into the cells next to the top wall
+// (2 beta g / h^2, the ghost 2g - inside of the viscous operator), 0 on the wall slot. C is the
+// component (= its index axis).
 template <int DIM, int C>
 __global__ void k_ns_source(double* __restrict__ f, const double* __restrict__ U, const double* __restrict__ V,
-                            const double* __restrict__ W, const double* __restrict__ P, NsGrid G, double dt,
-                            double beta, double lid_c) {
+                            const double* __restrict__ W, const double* __restrict__ P,
+                            const double* __restrict__ F, NsGrid G, double dt, double beta, double lid_c) {
   const double* vel[3] = {U, V, W};
   const double* __restrict__ phi = vel[C];
   const double h = G.h;
@@ -145,6 +146,7 @@ __global__ void k_ns_source(double* __restrict__ f, const double* __restrict__ U
     }
     const double gp = (P[idx + G.st[C]] - P[idx]) / h;
     double v = phi[idx] - dt * conv - dt * gp;
+    if (F) v = v + dt * F[idx];
     if (C != DIM - 1 && k[DIM - 1] == G.n[DIM - 1] - 1) v = v + 2.0 * beta * lid_c / (h * h);
     f[idx] = v;
   }
@@ -354,7 +356,8 @@ fas_status ns_create(int dim, const int n[3], double h, double Re, double dt, in
   return FAS_OK;
 }
 
-fas_status ns_projection_step(ns_ctx* c, double* const fields[8], fas_info info[4], double* div_max) {
+fas_status ns_projection_step(ns_ctx* c, double* const fields[8], const double* const force[3], fas_info info[4],
+                              double* div_max) {
   if (!c || !fields) return ns_fail(FAS_EINVAL, "ns_projection_step: null argument");
   const int dim = c->dim;
   double* cnew[3] = {fields[0], fields[2], dim == 3 ? fields[4] : nullptr};
@@ -371,23 +374,24 @@ fas_status ns_projection_step(ns_ctx* c, double* const fields[8], fas_info info[
   // viscous solves, one component at a time (each right-hand side reads only u^n and p^n)
   for (int a = 0; a < dim; ++a) {
     const double lid_a = c->lid[a];
+    const double* Fa = force ? force[a] : nullptr;
     if (dim == 2) {
       if (a == 0)
-        k_ns_source<2, 0><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], nullptr, Po, G, c->dt,
-                                                                  c->beta, lid_a);
+        k_ns_source<2, 0><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], nullptr, Po, Fa, G,
+                                                                  c->dt, c->beta, lid_a);
       else
-        k_ns_source<2, 1><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], nullptr, Po, G, c->dt,
-                                                                  c->beta, lid_a);
+        k_ns_source<2, 1><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], nullptr, Po, Fa, G,
+                                                                  c->dt, c->beta, lid_a);
     } else {
       if (a == 0)
-        k_ns_source<3, 0><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], cold[2], Po, G, c->dt,
-                                                                  c->beta, lid_a);
+        k_ns_source<3, 0><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], cold[2], Po, Fa, G,
+                                                                  c->dt, c->beta, lid_a);
       else if (a == 1)
-        k_ns_source<3, 1><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], cold[2], Po, G, c->dt,
-                                                                  c->beta, lid_a);
+        k_ns_source<3, 1><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], cold[2], Po, Fa, G,
+                                                                  c->dt, c->beta, lid_a);
       else
-        k_ns_source<3, 2><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], cold[2], Po, G, c->dt,
-                                                                  c->beta, lid_a);
+        k_ns_source<3, 2><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], cold[2], Po, Fa, G,
+                                                                  c->dt, c->beta, lid_a);
     }
     c->launches += 1;
     NS_CUDA_TRY(cudaGetLastError());

@@ -162,3 +162,83 @@ def test_projection_step_divergence_free(dim):
         assert div <= 1e-9 * max(rhs, 1.0)
     # the lid drags the fluid next to it in +x
     assert fields["U_old"][-1].mean() > 0
+
+
+# ---------------------------------------------------------------------------------------------
+# the paper's asymptotic-in-time convergence test of the first-order scheme (Sec. 4.4.3)
+# ---------------------------------------------------------------------------------------------
+
+def _mms_errors(n, nsteps, Re=10.0):
+    from workloads import mms_field, ns_mms
+    w = ns_mms(n, Re)
+    shape, h, dt = w["shape"], w["h"], 1.0 / nsteps
+    fields = {k: np.zeros(shape) for k in ("U_old", "U_new", "V_old", "V_new", "P_old", "P_new")}
+    prm = st.NSParams(Re=Re, dt=dt, lid=(0.0, 0.0, 0.0), solver=cc.Params(tol=1e-9, kmax=20, coarsest=4),
+                      pressure=cc.Params(tol=1e-9, kmax=60, coarsest=4, coarse_exact=True))
+    for k in range(nsteps):
+        t1 = (k + 1) * dt
+        st.projection_step(fields, shape, h, prm,
+                           force=[mms_field(w["force"][0], t1, 0), mms_field(w["force"][1], t1, 1)])
+    l2 = lambda a, b: float(np.sqrt(h * h * np.sum((a - b) ** 2)))  # noqa: E731
+    return (l2(fields["U_old"], mms_field(w["exact"][0], 1.0, 0)),
+            l2(fields["V_old"], mms_field(w["exact"][1], 1.0, 1)),
+            l2(fields["P_old"], mms_field(w["exact"]["p"], 1.0)))
+
+
+def test_mms_force_matches_symbolic_derivation():
+    """The body force of the manufactured solution against a symbolic derivation of
+    u_t + (u . grad) u + grad p - Lap u / Re."""
+    sp = pytest.importorskip("sympy")
+    from workloads import mms_field, ns_mms
+    x, y, t = sp.symbols("x y t")
+    Re = 10.0
+    p = sp.sin(t) * (sp.sin(sp.pi * y) - 2 / sp.pi)
+    u = sp.sin(t) * sp.sin(sp.pi * x) ** 2 * sp.sin(2 * sp.pi * y)
+    v = -sp.sin(t) * sp.sin(2 * sp.pi * x) * sp.sin(sp.pi * y) ** 2
+    assert sp.simplify(sp.diff(u, x) + sp.diff(v, y)) == 0
+    fu = sp.diff(u, t) + u * sp.diff(u, x) + v * sp.diff(u, y) + sp.diff(p, x) - (
+        sp.diff(u, x, 2) + sp.diff(u, y, 2)) / Re
+    fv = sp.diff(v, t) + u * sp.diff(v, x) + v * sp.diff(v, y) + sp.diff(p, y) - (
+        sp.diff(v, x, 2) + sp.diff(v, y, 2)) / Re
+    n = 16
+    w = ns_mms(n, Re)
+    h = 1.0 / n
+    fuf = sp.lambdify((x, y, t), fu, "numpy")
+    fvf = sp.lambdify((x, y, t), fv, "numpy")
+    uf, vf, pf = (sp.lambdify((x, y, t), e, "numpy") for e in (u, v, p))
+    c = (np.arange(n) + 0.5) * h
+    f = (np.arange(n) + 1.0) * h
+    for tv in (0.3, 1.0):
+        Xu, Yu = np.meshgrid(f, c)  # u points: x on faces, y at centres
+        Xv, Yv = np.meshgrid(c, f)
+        Xp, Yp = np.meshgrid(c, c)
+        fu_ref = fuf(Xu, Yu, tv)
+        fu_ref[:, -1] = 0.0
+        fv_ref = fvf(Xv, Yv, tv)
+        fv_ref[-1, :] = 0.0
+        np.testing.assert_allclose(mms_field(w["force"][0], tv, 0), fu_ref, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(mms_field(w["force"][1], tv, 1), fv_ref, rtol=0, atol=1e-12)
+        eu = uf(Xu, Yu, tv)
+        eu[:, -1] = 0.0
+        np.testing.assert_allclose(mms_field(w["exact"][0], tv, 0), eu, atol=1e-14)
+        ev = vf(Xv, Yv, tv)
+        ev[-1, :] = 0.0
+        np.testing.assert_allclose(mms_field(w["exact"][1], tv, 1), ev, atol=1e-14)
+        np.testing.assert_allclose(mms_field(w["exact"]["p"], tv), pf(Xp, Yp, tv) + 0 * Xp, atol=1e-14)
+
+
+@pytest.mark.slow
+def test_projection_step_reproduces_paper_first_order_table():
+    """Table first-convergence-test (Sec. 4.4.3, 4096^2): the oracle's errors at 128^2 and 256^2,
+    Richardson-extrapolated in h (spatial error O(h^2)), reproduce the printed u, v, p errors at
+    dt = 1/10 and 1/20 to 1 % (printed to 3 digits), and the time order is about 1."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "ns_first_order_mms.json")))
+    for row, nsteps in enumerate((10, 20)):
+        e128 = _mms_errors(128, nsteps)
+        e256 = _mms_errors(256, nsteps)
+        for k, key in enumerate(("err_u", "err_v", "err_p")):
+            ext = e256[k] + (e256[k] - e128[k]) / 3.0
+            ref = g[key][row]
+            assert abs(ext - ref) <= 0.01 * ref, (key, nsteps, ext, ref)

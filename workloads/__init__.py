@@ -239,3 +239,65 @@ def ns_cavity(n: int = 256, dim: int = 3, nsteps: int = 20):
     fields["P_old"] = np.zeros(shape)
     fields["P_new"] = np.zeros(shape)
     return dict(shape=shape, h=1.0 / n, Re=100.0, dt=1e-3, nsteps=nsteps, lid=(1.0, 0.0, 0.0), fields=fields)
+
+
+# ---------------------------------------------------------------------------------------------
+# the manufactured Navier-Stokes solution of the paper's asymptotic-in-time test (Sec. 4.4.3)
+# ---------------------------------------------------------------------------------------------
+
+def _sin2(t):
+    return np.sin(t) ** 2
+
+
+def ns_mms(n: int, Re: float = 10.0) -> dict:
+    """On [0,1]^2 with n x n cells: p = sin t (sin(pi y) - 2/pi), u = sin t sin^2(pi x) sin(2 pi y),
+    v = -sin t sin(2 pi x) sin^2(pi y), divergence free and 0 on the walls; the body force is
+    F = u_t + (u . grad) u + grad p - (1/Re) Lap u of that solution. Every field is a sum of terms
+    c(t) * outer(Y(y), X(x)) evaluated at its own points: u on x-faces (x = (i+1) h, y = (j+1/2) h),
+    v on y-faces, p at cell centres. Returns 'exact' and 'force' term lists per component (0 = u,
+    1 = v, 'p' = pressure)."""
+    h = 1.0 / n
+    c = (np.arange(n) + 0.5) * h  # cell centres
+    f = (np.arange(n) + 1.0) * h  # faces 1..n (slot s = face s+1)
+    pi = np.pi
+    s1, s2, cs = np.sin, _sin2, np.cos
+    one = np.ones(n)
+    exact = {
+        0: [(s1, np.sin(2 * pi * c), np.sin(pi * f) ** 2)],
+        1: [(s1, -np.sin(pi * f) ** 2, np.sin(2 * pi * c))],
+        "p": [(s1, np.sin(pi * c) - 2.0 / pi, one)],
+    }
+    # u at (x = f, y = c)
+    xu, yu = f, c
+    force_u = [
+        (cs, np.sin(2 * pi * yu), np.sin(pi * xu) ** 2),                                        # u_t
+        (s2, np.sin(2 * pi * yu) ** 2, pi * np.sin(2 * pi * xu) * np.sin(pi * xu) ** 2),       # u u_x
+        (s2, 2 * pi * np.sin(pi * yu) ** 2 * np.cos(2 * pi * yu),
+         -np.sin(2 * pi * xu) * np.sin(pi * xu) ** 2),                                         # v u_y
+        (s1, np.sin(2 * pi * yu), -2 * pi ** 2 * np.cos(2 * pi * xu) / Re),                    # -u_xx/Re
+        (s1, np.sin(2 * pi * yu), 4 * pi ** 2 * np.sin(pi * xu) ** 2 / Re),                    # -u_yy/Re
+    ]
+    # v at (x = c, y = f)
+    xv, yv = c, f
+    force_v = [
+        (cs, np.sin(pi * yv) ** 2, -np.sin(2 * pi * xv)),                                      # v_t
+        (s2, np.sin(2 * pi * yv) * np.sin(pi * yv) ** 2,
+         -2 * pi * np.sin(pi * xv) ** 2 * np.cos(2 * pi * xv)),                                # u v_x
+        (s2, np.sin(pi * yv) ** 2 * np.sin(2 * pi * yv), pi * np.sin(2 * pi * xv) ** 2),       # v v_y
+        (s1, pi * np.cos(pi * yv), np.ones(n)),                                                # p_y
+        (s1, np.sin(pi * yv) ** 2, -4 * pi ** 2 * np.sin(2 * pi * xv) / Re),                   # -v_xx/Re
+        (s1, np.cos(2 * pi * yv), 2 * pi ** 2 * np.sin(2 * pi * xv) / Re),                     # -v_yy/Re
+    ]
+    return dict(shape=(n, n), h=h, Re=Re, exact=exact, force={0: force_u, 1: force_v})
+
+
+def mms_field(terms, t: float, comp=None) -> np.ndarray:
+    """Sum of c(t) outer(Y, X) over the terms (numpy order (y, x)); a velocity component's far wall
+    slot is set to 0 (its wall value)."""
+    out = None
+    for fn, Y, X in terms:
+        term = float(fn(t)) * np.multiply.outer(Y, X)
+        out = term if out is None else out + term
+    if comp is not None:
+        zero_wall_slot(out, comp)
+    return out

@@ -433,18 +433,20 @@ def secondary_workloads(dev, stream):
     del u0, f, u, res
     torch.cuda.empty_cache()
 
-    # NS: first-order projection, lid-driven cavity 256^3, Re 100, dt 1e-3, 20 steps from rest
+    # NS: first- and second-order projection, lid-driven cavity 256^3, Re 100, dt 1e-3, 20 steps from rest
     w = ns_cavity(n=256, dim=3, nsteps=20)
     shape, nsteps = w["shape"], w["nsteps"]
     cells = int(np.prod(shape))
     zero = torch.zeros(shape, dtype=torch.float64, device=dev)
-    ns_res = {}
-    for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
+    for order in (1, 2):
+      ns_res = {}
+      for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
         sp = fas.fas_default_params()
         sp.precision, sp.kmax, sp.coarsest = prec, 40, 4
         pp = fas.fas_default_params()
         pp.precision, pp.kmax, pp.coarsest, pp.coarse_exact = prec, 60, 4, 1
-        ns = fas.ns_create(shape, w["h"], w["Re"], w["dt"], lid=w["lid"], solver=sp, pressure=pp, stream=stream)
+        ns = fas.ns_create(shape, w["h"], w["Re"], w["dt"], lid=w["lid"], order=order, solver=sp, pressure=pp,
+                           stream=stream)
         flds = {k: zero.clone() for k in w["fields"]}
 
         def run():
@@ -461,11 +463,13 @@ def secondary_workloads(dev, stream):
         _, dmax = fas.ns_projection_step(ns, flds, want_div=True)
         ns_res[name] = {"ms_per_step": ms / nsteps, "vcycles_per_step_u_v_w_p": [c / nsteps for c in tot],
                         "Mcells_vcycles_per_s": mc(cells, sum(tot), ms), "div_max_after": dmax,
-                        "U": flds["U_old"].clone()}
+                        "U": (flds["U_old"] if order == 1 else flds["U_new"]).clone()}
         del flds
         fas.ns_destroy(ns)
-    out["ns_cavity_256"] = {
-        "workload": "ns-first-order-projection-lid-cavity-256^3-Re100-dt1e-3-20steps-WENO3-tol1e-10",
+      key = "ns_cavity_256" if order == 1 else "ns_cavity_256_order2"
+      out[key] = {
+        "workload": "ns-%s-order-projection-lid-cavity-256^3-Re100-dt1e-3-20steps-WENO3-tol1e-10"
+                    % ("first" if order == 1 else "second"),
         "mixed": {k: v for k, v in ns_res["mixed"].items() if k != "U"},
         "fp64": {k: v for k, v in ns_res["fp64"].items() if k != "U"},
         "speedup_mixed_vs_fp64_time": ns_res["fp64"]["ms_per_step"] / ns_res["mixed"]["ms_per_step"],

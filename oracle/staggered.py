@@ -370,8 +370,14 @@ def advecting_velocity(vel, comp, a):
 
 def convection(vel, comp, h, lid):
     """(u . grad) of component comp at its unknowns (WENO3, upwinded by the advecting velocity)."""
-    dim = len(vel)
-    phi = vel[comp]
+    return convection_of(vel[comp], vel, comp, h, lid)
+
+
+def convection_of(phi, advect, comp, h, lid):
+    """(a . grad) phi for the face field phi of component comp: WENO3 derivatives of phi, upwinded by
+    the advecting velocity, whose component a is interpolated from advect[a] (a != comp) or is phi
+    itself (a == comp)."""
+    dim = phi.ndim
     fc = dim - 1 - comp
     out = np.zeros(phi.shape)
     for a in range(dim):
@@ -387,7 +393,7 @@ def convection(vel, comp, h, lid):
             dm = np.concatenate([dm, pad], axis=ax)
             dp = np.concatenate([dp, pad], axis=ax)
         else:
-            adv = advecting_velocity(vel, comp, a)
+            adv = advecting_velocity(advect, comp, a)
         out = out + np.where(adv > 0.0, adv * dm, adv * dp)
     out[tuple(slice(None) if k != fc else phi.shape[fc] - 1 for k in range(dim))] = 0.0
     return out
@@ -463,4 +469,55 @@ def projection_step(fields: dict, shape, h, prm: NSParams, force=None):
         fields[nm + "_old"][...] = vel_t[comp] - dt * pressure_gradient(fields["P_new"], comp, h)
     fields["P_old"] += fields["P_new"]
     div = divergence([fields[nm + "_old"] for nm in names], h)
+    return infos, float(np.max(np.abs(div))), float(np.max(np.abs(rhs)))
+
+
+def projection_step2(fields: dict, shape, h, prm: NSParams, force=None):
+    """Scheme second-1..4 (Sec. 4.3) in the order of the memory-efficient 8-field table of the
+    second-order scheme. On entry C_new holds c^n and C_old holds c^{n-1} (both c^0 at the first step);
+    for each component c in turn:
+        f_c = c^n - dt (a . grad) cbar + (dt / 2Re) Lap c^n - dt (grad p^n)_c (+ dt F_c)   cbar = (3c^n - c^{n-1})/2
+              advecting a: (a^n + a~^{n+1})/2 for the components already solved in this step,
+              (3a^n - a^{n-1})/2 for the others (cbar itself along c)
+        C_old <- C_new (the lagged update), then (I - dt/2Re Lap) c~ = f_c from c^n into C_new;
+    then -dt Lap p~ = -div u~ into P_new, c^{n+1} = c~ - dt (grad p~)_c in C_new, P_old += P_new.
+    The lid enters once for the implicit and once for the explicit half of the viscous term, 2 beta g /
+    h^2 each with beta = dt / 2Re. force: per component, the body force at t^{n+1/2} (reading)."""
+    dim = len(shape)
+    names = ["U", "V", "W"][:dim]
+    dt = prm.dt
+    beta = dt / (2.0 * prm.Re)
+    sol = prm.solver or cc.Params(tol=1e-10, kmax=40, coarsest=4)
+    psol = prm.pressure or cc.Params(tol=1e-10, kmax=60, coarsest=4, coarse_exact=True)
+    p_n = fields["P_old"]
+    infos = []
+    for comp, nm in enumerate(names):
+        cur = [fields[m + "_new"] for m in names]
+        old = [fields[m + "_old"] for m in names]
+        cbar = 0.5 * (3.0 * cur[comp] - old[comp])
+        advect = []
+        for a in range(dim):
+            if a < comp:
+                advect.append(0.5 * (old[a] + cur[a]))  # a^n (lagged into C_old) and a~^{n+1}
+            else:
+                advect.append(0.5 * (3.0 * cur[a] - old[a]))
+        op = FaceOperator(shape, h, 1.0, beta, comp)
+        lap = -apply_A_face(FaceOperator(shape, h, 0.0, 1.0, comp), cur[comp])
+        f = cur[comp] - dt * convection_of(cbar, advect, comp, h, prm.lid) + beta * lap \
+            - dt * pressure_gradient(p_n, comp, h)
+        if force is not None and force[comp] is not None:
+            f = f + dt * np.asarray(force[comp], dtype=np.float64)
+        f = f + 2.0 * lid_rhs(shape, comp, beta, h, prm.lid)
+        f[frozen_slice(op)] = 0.0
+        fields[nm + "_old"][...] = cur[comp]
+        infos.append(solve_face(build_levels_face(op, sol.coarsest), fields[nm + "_new"], f, sol))
+    vel_t = [fields[nm + "_new"] for nm in names]
+    rhs = -divergence(vel_t, h)
+    pop = cc.Operator(shape, h, 0.0, dt, 1.0)
+    fields["P_new"][...] = 0.0
+    infos.append(cc.solve(cc.build_levels(pop, psol.coarsest), fields["P_new"], rhs, psol))
+    for comp, nm in enumerate(names):
+        fields[nm + "_new"][...] = vel_t[comp] - dt * pressure_gradient(fields["P_new"], comp, h)
+    fields["P_old"] += fields["P_new"]
+    div = divergence([fields[nm + "_new"] for nm in names], h)
     return infos, float(np.max(np.abs(div))), float(np.max(np.abs(rhs)))

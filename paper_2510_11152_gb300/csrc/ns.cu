@@ -152,6 +152,95 @@ __global__ void k_ns_source(double* __restrict__ f, const double* __restrict__ U
   }
 }
 
+// Second-order scheme (Scheme second-1..4, the lagged 8-field table): the right-hand side of
+// (I - dt/2Re Lap) c~ = f_C with
+//   f_C = c^n - dt (a . grad) cbar + (dt/2Re) Lap c^n - dt (p^n_{s+1} - p^n_s)/h + dt F (+ lid)
+// where cbar = (3 c^n - c^{n-1})/2 is differentiated by WENO3, and the advecting component a is
+// (a^n + a~^{n+1})/2 for a < C (already solved this step: a^n lagged into OLD, a~ in CUR) and
+// (3 a^n - a^{n-1})/2 otherwise (CUR = a^n, OLD = a^{n-1}). The lid enters twice (implicit and
+// explicit halves of the viscous term, 2 beta g / h^2 each, beta = dt/2Re).
+template <int DIM, int C>
+__global__ void k_ns_source2(double* __restrict__ f, const double* __restrict__ U, const double* __restrict__ Uo,
+                             const double* __restrict__ V, const double* __restrict__ Vo,
+                             const double* __restrict__ W, const double* __restrict__ Wo,
+                             const double* __restrict__ P, const double* __restrict__ F, NsGrid G, double dt,
+                             double beta, double lid_c) {
+  const double* cur[3] = {U, V, W};
+  const double* old[3] = {Uo, Vo, Wo};
+  const double* __restrict__ cc = cur[C];
+  const double* __restrict__ co = old[C];
+  const double h = G.h;
+  for (int64_t idx = ns_tid(); idx < G.cells; idx += ns_stride()) {
+    int k[3];
+    ns_coords(G, idx, k);
+    if (k[C] == G.n[C] - 1) {
+      f[idx] = 0.0;
+      continue;
+    }
+    auto cbar = [&](int64_t q) { return 0.5 * (3.0 * cc[q] - co[q]); };
+    double conv = 0.0, lap = 0.0;
+    const double c0 = cc[idx];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int64_t st = G.st[a];
+      const int64_t line = idx - (int64_t)k[a] * st;
+      const int n = G.n[a];
+      double v[5];
+      if (a == C) {
+#pragma unroll
+        for (int s = -2; s <= 2; ++s) {
+          int F2 = k[a] + 1 + s;  // face index, odd continuation beyond the walls
+          double sg = 1.0;
+          if (F2 < 0) {
+            F2 = -F2;
+            sg = -1.0;
+          } else if (F2 > n) {
+            F2 = 2 * n - F2;
+            sg = -1.0;
+          }
+          v[s + 2] = F2 == 0 ? 0.0 : sg * cbar(line + (int64_t)(F2 - 1) * st);
+        }
+        const double lo = k[a] > 0 ? cc[idx - st] : 0.0;
+        lap += (lo - 2.0 * c0) + cc[idx + st];
+      } else {
+        const double g_hi = a == DIM - 1 ? lid_c : 0.0;
+#pragma unroll
+        for (int s = -2; s <= 2; ++s) {
+          const int cidx = k[a] + s;
+          if (cidx < 0) v[s + 2] = -cbar(line + (int64_t)(-cidx - 1) * st);
+          else if (cidx >= n) v[s + 2] = 2.0 * g_hi - cbar(line + (int64_t)(2 * n - 1 - cidx) * st);
+          else v[s + 2] = cbar(line + (int64_t)cidx * st);
+        }
+        const double lo = k[a] > 0 ? cc[idx - st] : -c0;
+        const double hi = k[a] < n - 1 ? cc[idx + st] : -c0;
+        lap += (hi - c0) - (c0 - lo);
+      }
+      const double d1 = (v[1] - v[0]) / h, d2 = (v[2] - v[1]) / h, d3 = (v[3] - v[2]) / h, d4 = (v[4] - v[3]) / h;
+      const double dm = weno3(d1, d2, d3);
+      const double dp = weno3(d4, d3, d2);
+      double adv;
+      if (a == C) {
+        adv = cbar(idx);
+      } else {
+        const double* __restrict__ Ac = cur[a];
+        const double* __restrict__ Ao = old[a];
+        auto A = [&](int64_t q) { return a < C ? 0.5 * (Ao[q] + Ac[q]) : 0.5 * (3.0 * Ac[q] - Ao[q]); };
+        const int64_t sa = G.st[a], sc = G.st[C];
+        const bool in = k[a] > 0;
+        const double lo = 0.5 * ((in ? A(idx - sa) : 0.0) + A(idx));
+        const double hi = 0.5 * ((in ? A(idx - sa + sc) : 0.0) + A(idx + sc));
+        adv = 0.5 * (lo + hi);
+      }
+      conv = conv + (adv > 0.0 ? adv * dm : adv * dp);
+    }
+    const double gp = (P[idx + G.st[C]] - P[idx]) / h;
+    double v = c0 - dt * conv + beta * (lap / (h * h)) - dt * gp;
+    if (F) v = v + dt * F[idx];
+    if (C != DIM - 1 && k[DIM - 1] == G.n[DIM - 1] - 1) v = v + 2.0 * (2.0 * beta * lid_c / (h * h));
+    f[idx] = v;
+  }
+}
+
 // rhs = -div u over the cells, wall faces 0 (face k+1 of a cell is slot k, face k slot k-1).
 template <int DIM>
 __global__ void k_ns_neg_div(double* __restrict__ rhs, const double* __restrict__ U, const double* __restrict__ V,
@@ -173,11 +262,11 @@ __global__ void k_ns_neg_div(double* __restrict__ rhs, const double* __restrict_
 
 // c_old = c_new - dt (p_{s+1} - p_s)/h for every component (the wall slot keeps c_new, which is 0),
 // p_old += p_new. One pass over the eight fields.
+// (out may equal in: every element is read and written by the same thread.)
 template <int DIM>
-__global__ void k_ns_project(double* __restrict__ Uo, double* __restrict__ Vo, double* __restrict__ Wo,
-                             const double* __restrict__ Un, const double* __restrict__ Vn,
-                             const double* __restrict__ Wn, double* __restrict__ Po, const double* __restrict__ Pn,
-                             NsGrid G, double dt) {
+__global__ void k_ns_project(double* Uo, double* Vo, double* Wo, const double* Un, const double* Vn,
+                             const double* Wn, double* __restrict__ Po, const double* __restrict__ Pn, NsGrid G,
+                             double dt) {
   double* out[3] = {Uo, Vo, Wo};
   const double* in[3] = {Un, Vn, Wn};
   for (int64_t idx = ns_tid(); idx < G.cells; idx += ns_stride()) {
@@ -241,7 +330,8 @@ __global__ void k_ns_finish_max(const double* partials, int nb, double* out) {
 struct ns_ctx {
   int dim = 2;
   NsGrid G{};
-  double Re = 0.0, dt = 0.0, beta = 0.0;
+  double Re = 0.0, dt = 0.0, beta = 0.0;  // beta: dt/Re (first order) or dt/2Re (second order)
+  int order = 1;
   double lid[3] = {0.0, 0.0, 0.0};
   cudaStream_t stream = nullptr;
   fas_ctx* vel[3] = {nullptr, nullptr, nullptr};
@@ -257,6 +347,42 @@ struct ns_ctx {
 namespace {
 
 bool pow2_at_least(int v, int lo) { return v >= lo && (v & (v - 1)) == 0; }
+
+template <int DIM, int C>
+void source1(ns_ctx* c, double* const* un, const double* P, const double* F, double lid) {
+  k_ns_source<DIM, C><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, un[0], un[1], DIM == 3 ? un[2] : nullptr, P, F,
+                                                              c->G, c->dt, c->beta, lid);
+}
+
+void launch_source1(ns_ctx* c, int a, double* const* un, const double* P, const double* F, double lid) {
+  if (c->dim == 2) {
+    if (a == 0) source1<2, 0>(c, un, P, F, lid);
+    else source1<2, 1>(c, un, P, F, lid);
+  } else {
+    if (a == 0) source1<3, 0>(c, un, P, F, lid);
+    else if (a == 1) source1<3, 1>(c, un, P, F, lid);
+    else source1<3, 2>(c, un, P, F, lid);
+  }
+}
+
+template <int DIM, int C>
+void source2(ns_ctx* c, double* const* cur, double* const* old, const double* P, const double* F, double lid) {
+  k_ns_source2<DIM, C><<<c->nblocks, kNsBlock, 0, c->stream>>>(
+      c->ftmp, cur[0], old[0], cur[1], old[1], DIM == 3 ? cur[2] : nullptr, DIM == 3 ? old[2] : nullptr, P, F, c->G,
+      c->dt, c->beta, lid);
+}
+
+void launch_source2(ns_ctx* c, int a, double* const* cur, double* const* old, const double* P, const double* F,
+                    double lid) {
+  if (c->dim == 2) {
+    if (a == 0) source2<2, 0>(c, cur, old, P, F, lid);
+    else source2<2, 1>(c, cur, old, P, F, lid);
+  } else {
+    if (a == 0) source2<3, 0>(c, cur, old, P, F, lid);
+    else if (a == 1) source2<3, 1>(c, cur, old, P, F, lid);
+    else source2<3, 2>(c, cur, old, P, F, lid);
+  }
+}
 
 fas_status ns_check_solve(fas_status st, const char* what, fas_status* first) {
   if (st == FAS_OK) return FAS_OK;
@@ -280,12 +406,13 @@ fas_status ns_create(int dim, const int n[3], double h, double Re, double dt, in
     if (!pow2_at_least(n[a], 4)) return ns_fail(FAS_EINVAL, "ns_create: every n must be a power of two >= 4");
   if (!(h > 0.0) || !(Re > 0.0) || !(dt > 0.0) || !std::isfinite(h) || !std::isfinite(Re) || !std::isfinite(dt))
     return ns_fail(FAS_EINVAL, "ns_create: h, Re, dt must be positive");
-  if (order != 1) return ns_fail(FAS_EUNSUPPORTED, "ns_create: only the first-order projection scheme is built");
+  if (order != 1 && order != 2) return ns_fail(FAS_EUNSUPPORTED, "ns_create: order must be 1 or 2");
   ns_ctx* c = new ns_ctx();
   c->dim = dim;
   c->Re = Re;
   c->dt = dt;
-  c->beta = dt / Re;
+  c->order = order;
+  c->beta = order == 1 ? dt / Re : dt / (2.0 * Re);
   for (int a = 0; a < 3; ++a) c->lid[a] = lid ? lid[a] : 0.0;
   c->stream = (cudaStream_t)stream;
   NsGrid& G = c->G;
@@ -371,31 +498,22 @@ fas_status ns_projection_step(ns_ctx* c, double* const fields[8], const double* 
   const NsGrid& G = c->G;
   const size_t bytes = (size_t)G.cells * sizeof(double);
   fas_status first = FAS_OK;
-  // viscous solves, one component at a time (each right-hand side reads only u^n and p^n)
+  const bool second = c->order == 2;
+  // viscous solves, one component at a time
   for (int a = 0; a < dim; ++a) {
     const double lid_a = c->lid[a];
     const double* Fa = force ? force[a] : nullptr;
-    if (dim == 2) {
-      if (a == 0)
-        k_ns_source<2, 0><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], nullptr, Po, Fa, G,
-                                                                  c->dt, c->beta, lid_a);
-      else
-        k_ns_source<2, 1><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], nullptr, Po, Fa, G,
-                                                                  c->dt, c->beta, lid_a);
-    } else {
-      if (a == 0)
-        k_ns_source<3, 0><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], cold[2], Po, Fa, G,
-                                                                  c->dt, c->beta, lid_a);
-      else if (a == 1)
-        k_ns_source<3, 1><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], cold[2], Po, Fa, G,
-                                                                  c->dt, c->beta, lid_a);
-      else
-        k_ns_source<3, 2><<<c->nblocks, kNsBlock, 0, c->stream>>>(c->ftmp, cold[0], cold[1], cold[2], Po, Fa, G,
-                                                                  c->dt, c->beta, lid_a);
+    if (!second) {  // f from u^n (in C_old) and p^n; the solve starts from u^n copied into C_new
+      launch_source1(c, a, cold, Po, Fa, lid_a);
+    } else {  // f from c^n (C_new), c^{n-1} (C_old) and the solved a~ (C_new of a < C)
+      launch_source2(c, a, cnew, cold, Po, Fa, lid_a);
     }
     c->launches += 1;
     NS_CUDA_TRY(cudaGetLastError());
-    NS_CUDA_TRY(cudaMemcpyAsync(cnew[a], cold[a], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (!second)
+      NS_CUDA_TRY(cudaMemcpyAsync(cnew[a], cold[a], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    else  // the lagged update c^{n-1} <- c^n; C_new keeps c^n as the initial guess
+      NS_CUDA_TRY(cudaMemcpyAsync(cold[a], cnew[a], bytes, cudaMemcpyDeviceToDevice, c->stream));
     fas_info inf;
     const fas_status st = fas_solve(c->vel[a], cnew[a], c->ftmp, &inf);
     if (info) info[a] = inf;
@@ -415,20 +533,21 @@ fas_status ns_projection_step(ns_ctx* c, double* const fields[8], const double* 
     if (info) info[3] = inf;
     if (ns_check_solve(st, "pressure solve", &first) != FAS_OK) return st;
   }
-  // projection and pressure update
+  // projection and pressure update: u^{n+1} into C_old (first order) or in place in C_new (second)
+  double* const* out = second ? cnew : cold;
   if (dim == 2)
-    k_ns_project<2><<<c->nblocks, kNsBlock, 0, c->stream>>>(cold[0], cold[1], nullptr, cnew[0], cnew[1], nullptr, Po,
+    k_ns_project<2><<<c->nblocks, kNsBlock, 0, c->stream>>>(out[0], out[1], nullptr, cnew[0], cnew[1], nullptr, Po,
                                                             Pn, G, c->dt);
   else
-    k_ns_project<3><<<c->nblocks, kNsBlock, 0, c->stream>>>(cold[0], cold[1], cold[2], cnew[0], cnew[1], cnew[2], Po,
+    k_ns_project<3><<<c->nblocks, kNsBlock, 0, c->stream>>>(out[0], out[1], out[2], cnew[0], cnew[1], cnew[2], Po,
                                                             Pn, G, c->dt);
   c->launches += 1;
   NS_CUDA_TRY(cudaGetLastError());
   if (div_max) {
     if (dim == 2)
-      k_ns_div_max<2><<<c->nblocks, kNsBlock, 0, c->stream>>>(cold[0], cold[1], nullptr, G, c->partials);
+      k_ns_div_max<2><<<c->nblocks, kNsBlock, 0, c->stream>>>(out[0], out[1], nullptr, G, c->partials);
     else
-      k_ns_div_max<3><<<c->nblocks, kNsBlock, 0, c->stream>>>(cold[0], cold[1], cold[2], G, c->partials);
+      k_ns_div_max<3><<<c->nblocks, kNsBlock, 0, c->stream>>>(out[0], out[1], out[2], G, c->partials);
     k_ns_finish_max<<<1, 1024, 0, c->stream>>>(c->partials, c->nblocks, c->d_max);
     c->launches += 2;
     NS_CUDA_TRY(cudaMemcpyAsync(c->h_max, c->d_max, sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -620,7 +620,7 @@ int launch_ir_residual(fas_ctx* c, float* r32, const double* u, const double* b,
   const int64_t n = c->shape[0].cells();
   int g = grid_for(c, n);
   Prof pr(c, FAS_K_IR, 0, (double)n);
-  if (c->p.dim == 2 && ir_strip_supported(L))
+  if (ir_strip_supported(L))
     launch_ir_strip(r32, u, b, L, nsp, c->partials, c->sm_count, c->max_blocks, &g, c->stream);
   else if (c->p.dim == 2)
     k_ir_residual<2><<<g, kBlock, 0, c->stream>>>(r32, u, b, L, nsp, c->partials);

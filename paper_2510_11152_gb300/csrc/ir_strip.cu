@@ -1,5 +1,5 @@
 // ir_strip.cu -- the float64 refinement residual r32 = (float)(b - A u) of the mixed-precision solve
-// for 2D cell-centred levels with a constant diffusivity, and its norm.
+// with a constant diffusivity, and its norm: 2D cell-centred levels, and 3D levels (cells or faces).
 //
 // GB300 runs float64 arithmetic at 1/64 of the float32 rate, which makes this kernel, not HBM, the
 // bottleneck of a refinement step when evaluated as five float64 operations per cell. Here the
@@ -275,16 +275,240 @@ __global__ void __launch_bounds__(kIrThreads, 2)
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// ------------------------------------------------------------------------------------------------
+// 3D (cell-centred or face grids, constant kappa): a warp owns a 128-column strip of one row y and
+// walks a segment of planes z with the planes z-1, z, z+1 of its row unpacked in registers; the rows
+// y-1 and y+1 of the current plane are read by the neighbouring warps of the block too (eight
+// consecutive rows per block), so they come from L1. Exact zeros (the wall slots of face grids, a
+// fluid at rest) are exact values here: significand 0, outside the exponent range.
+// ------------------------------------------------------------------------------------------------
+constexpr int kIr3Rows = kIrWarps;  // rows y per block
+
+struct IrRow3 {
+  int64_t sig[4];
+  int E[4];
+  uint64_t halo;
+  int lo, hi;
+  bool present;
+};
+
+__device__ __forceinline__ void unpack_z(uint64_t raw, int64_t& sig, int& E, int& lo, int& hi, bool& bad) {
+  E = (int)((raw >> 52) & 0x7FF);
+  const bool zero = (raw << 1) == 0ull;
+  const int64_t m = (int64_t)((raw & kMant52) | (1ull << 52));
+  sig = zero ? 0 : ((raw >> 63) ? -m : m);
+  if (!zero) {
+    lo = min(lo, E);
+    hi = max(hi, E);
+    bad = bad || bad_exp(E);
+  }
+}
+
+// sig 2^(E - Eref); zeros (sig 0) give 0 whatever their exponent field
+__device__ __forceinline__ int64_t align_z(int64_t sig, int E, int Eref) {
+  return (int64_t)((uint64_t)sig << ((E - Eref) & 63));
+}
+
+__device__ __forceinline__ void load_row3(IrRow3& R, const double* __restrict__ u, int64_t base, bool present,
+                                          int x0, int nx, int lane, bool halos) {
+  R.present = present;
+  int lo = kExpNone, hi = -kExpNone;
+  bool bad = false;
+  R.halo = 0ull;
+  if (present) {
+    const double2 a = reinterpret_cast<const double2*>(u + base)[0];
+    const double2 b = reinterpret_cast<const double2*>(u + base)[1];
+    const uint64_t v[4] = {(uint64_t)__double_as_longlong(a.x), (uint64_t)__double_as_longlong(a.y),
+                           (uint64_t)__double_as_longlong(b.x), (uint64_t)__double_as_longlong(b.y)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) unpack_z(v[k], R.sig[k], R.E[k], lo, hi, bad);
+    if (halos && ((lane == 0 && x0 > 0) || (lane == 31 && x0 + 4 < nx))) {
+      R.halo = (uint64_t)__double_as_longlong(u[lane == 0 ? base - 1 : base + 4]);
+      int64_t hs;
+      int Eh;
+      unpack_z(R.halo, hs, Eh, lo, hi, bad);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      R.sig[k] = 0;
+      R.E[k] = 0;
+    }
+  }
+  R.lo = __reduce_min_sync(kAll, bad ? -kExpNone : lo);
+  R.hi = __reduce_max_sync(kAll, hi);
+}
+
+__global__ void __launch_bounds__(kIrThreads, 2)
+    k_ir_strip3(float* __restrict__ r32, const double* __restrict__ u, const double* __restrict__ b,
+                LevelDesc<double> L, const float* nsp, double* partials, int zseg) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  const int nstrips = nx / kIrCols;
+  const int nyg = ny / kIr3Rows;
+  const int nzs = (nz + zseg - 1) / zseg;
+  const int ntasks = nstrips * nyg * nzs;
+  const float nscale = nsp ? *nsp : 1.f;
+  float acc = 0.f;
+  for (int task = blockIdx.x; task < ntasks; task += gridDim.x) {
+    const int sx = task % nstrips;
+    const int rest = task / nstrips;
+    const int y = (rest % nyg) * kIr3Rows + warp;
+    const int z0 = (rest / nyg) * zseg, z1 = min(nz, z0 + zseg);
+    const int x0 = sx * kIrCols + 4 * lane;
+    const int64_t rowb = (int64_t)y * sy + x0;
+    IrRow3 P, C, N;
+    load_row3(P, u, rowb + (int64_t)(z0 - 1) * sz, z0 - 1 >= 0, x0, nx, lane, true);
+    load_row3(C, u, rowb + (int64_t)z0 * sz, true, x0, nx, lane, true);
+    for (int z = z0; z < z1; ++z) {
+      load_row3(N, u, rowb + (int64_t)(z + 1) * sz, z + 1 < nz, x0, nx, lane, true);
+      const int64_t cb = rowb + (int64_t)z * sz;
+      IrRow3 S, T;  // rows y-1 and y+1 of plane z
+      load_row3(S, u, cb - sy, y > 0, x0, nx, lane, false);
+      load_row3(T, u, cb + sy, y < ny - 1, x0, nx, lane, false);
+      const double2 b01 = reinterpret_cast<const double2*>(b + cb)[0];
+      const double2 b23 = reinterpret_cast<const double2*>(b + cb)[1];
+      const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
+      double r[4];
+      const int Eref = min(min(C.lo, min(P.lo, N.lo)), min(S.lo, T.lo));
+      const int Etop = max(max(C.hi, max(P.hi, N.hi)), max(S.hi, T.hi));
+      // an all-zero stencil window has Eref = kExpNone: any exponent works, use 1
+      const int Eb = Eref == kExpNone ? 1 : Eref;
+      bool exact = Etop - Eref <= kMaxExpSpread || Eref == kExpNone;
+      if (exact) {
+        int64_t Xc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Xc[k] = align_z(C.sig[k], C.E[k], Eb);
+        long long wl = __shfl_up_sync(kAll, (long long)Xc[3], 1);
+        long long er = __shfl_down_sync(kAll, (long long)Xc[0], 1);
+        if (lane == 0 || lane == 31) {
+          int64_t hs = 0;
+          int Eh = 0, l0 = 0, h0 = 0;
+          bool bd = false;
+          unpack_z(C.halo, hs, Eh, l0, h0, bd);
+          const int64_t hx = align_z(hs, Eh, Eb);
+          if (lane == 0) wl = hx;
+          else er = hx;
+        }
+        const bool inner = y > 0 && y < ny - 1 && z > 0 && z < nz - 1;  // the same on every lane
+        int64_t Sx[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int64_t Xw = k ? Xc[k - 1] : (int64_t)wl;
+          const int64_t Xe = k < 3 ? Xc[k + 1] : (int64_t)er;
+          const int64_t V = (align_z(S.sig[k], S.E[k], Eb) + align_z(T.sig[k], T.E[k], Eb)) +
+                            (align_z(P.sig[k], P.E[k], Eb) + align_z(N.sig[k], N.E[k], Eb));
+          int M = 6;
+          if (!inner || (k == 0 && x0 == 0) || (k == 3 && x0 + 4 == nx)) {
+            const int cls = bclass<3>(x0 + k, y, z, nx, ny, nz);
+            M = (int)L.mt[cls];
+          }
+          Sx[k] = (Xw + Xe) + V - (int64_t)M * Xc[k];
+        }
+        bool small = true;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          small = small && (uint64_t)(Sx[k] + ((1ll << 53) - 1)) < (1ull << 54) - 1ull;
+        bool ok = true;
+        if (__all_sync(kAll, small)) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            double Sd;
+            ok = fixed_to_f64_small(Sx[k], Eb, &Sd) && ok;
+            r[k] = fma(L.c, Sd, fma(-L.alpha, as_d(repack(C.sig[k], C.E[k])), bv[k]));
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            double Sd;
+            ok = fixed_to_f64(Sx[k], Eb, &Sd) && ok;
+            r[k] = fma(L.c, Sd, fma(-L.alpha, as_d(repack(C.sig[k], C.E[k])), bv[k]));
+          }
+        }
+        exact = !__any_sync(kAll, !ok);
+      }
+      if (!exact) {  // the float64 point equation, as in residual_point, from the values in memory
+        const double2* pc = reinterpret_cast<const double2*>(u + cb);
+        const double c4[4] = {pc[0].x, pc[0].y, pc[1].x, pc[1].y};
+        double wv = __shfl_up_sync(kAll, c4[3], 1);
+        double ev = __shfl_down_sync(kAll, c4[0], 1);
+        if (lane == 0 && x0 > 0) wv = u[cb - 1];
+        if (lane == 31 && x0 + 4 < nx) ev = u[cb + 4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int x = x0 + k;
+          const int64_t q = cb + k;
+          const double w = x > 0 ? (k ? c4[k - 1] : wv) : 0.0;
+          const double e = x < nx - 1 ? (k < 3 ? c4[k + 1] : ev) : 0.0;
+          const double sv = y > 0 ? u[q - sy] : 0.0;
+          const double nv = y < ny - 1 ? u[q + sy] : 0.0;
+          const double bo = z > 0 ? u[q - sz] : 0.0;
+          const double to = z < nz - 1 ? u[q + sz] : 0.0;
+          const double nb = ((w + e) + (sv + nv)) + (bo + to);
+          const int cls = bclass<3>(x, y, z, nx, ny, nz);
+          r[k] = fma(L.c, nb, fma(-L.d[cls], c4[k], bv[k]));
+        }
+      }
+      // frozen wall slots of a face grid: residual 0
+      if (L.fax >= 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if ((L.fax == 0 && x0 + k == nx - 1) || (L.fax == 1 && y == ny - 1) || (L.fax == 2 && z == nz - 1))
+            r[k] = 0.0;
+      }
+      float4 o;
+      const bool nrm = f32_normal_range(r[0]) && f32_normal_range(r[1]) && f32_normal_range(r[2]) &&
+                       f32_normal_range(r[3]);
+      if (__all_sync(kAll, nrm)) {
+        o.x = f64_to_f32_rn_normal(r[0]);
+        o.y = f64_to_f32_rn_normal(r[1]);
+        o.z = f64_to_f32_rn_normal(r[2]);
+        o.w = f64_to_f32_rn_normal(r[3]);
+      } else {
+        o.x = f64_to_f32_rn_bits(r[0]);
+        o.y = f64_to_f32_rn_bits(r[1]);
+        o.z = f64_to_f32_rn_bits(r[2]);
+        o.w = f64_to_f32_rn_bits(r[3]);
+      }
+      *reinterpret_cast<float4*>(r32 + cb) = o;
+      const float s0 = o.x * nscale, s1 = o.y * nscale, s2 = o.z * nscale, s3 = o.w * nscale;
+      acc = fmaf(s0, s0, acc);
+      acc = fmaf(s1, s1, acc);
+      acc = fmaf(s2, s2, acc);
+      acc = fmaf(s3, s3, acc);
+      P = C;
+      C = N;
+    }
+  }
+  const double s = block_sum((double)acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 }  // namespace
 
 bool ir_strip_supported(const LevelDesc<double>& L) {
-  return L.nz == 1 && L.fax < 0 && !L.varkappa && L.nx % kIrCols == 0 && L.ny >= 1;
+  if (L.varkappa || L.nx % kIrCols != 0) return false;
+  if (L.nz == 1) return L.fax < 0 && L.ny >= 1;
+  return L.ny % kIr3Rows == 0;
 }
 
 cudaError_t launch_ir_strip(float* r32, const double* u, const double* b, const LevelDesc<double>& L,
                             const float* nsp, double* partials, int sm_count, int max_blocks, int* nblocks,
                             cudaStream_t stream) {
   const int nstrips = L.nx / kIrCols;
+  if (L.nz > 1) {
+    // blocks of eight rows y; z segments sized for about four blocks per SM, 8..128 planes each
+    const int64_t cols = (int64_t)nstrips * (L.ny / kIr3Rows);
+    const int64_t per = std::max<int64_t>(1, ((int64_t)sm_count * 4) / cols);
+    const int zseg = (int)std::min<int64_t>(128, std::max<int64_t>(8, (L.nz + per - 1) / per));
+    const int64_t ntasks = cols * ((L.nz + zseg - 1) / zseg);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(max_blocks, ntasks));
+    *nblocks = blocks;
+    k_ir_strip3<<<blocks, kIrThreads, 0, stream>>>(r32, u, b, L, nsp, partials, zseg);
+    return cudaGetLastError();
+  }
   // segments: about four blocks of eight warps per SM, 16..256 rows each (two halo rows per segment)
   const int64_t target = (int64_t)sm_count * 4 * kIrWarps;
   const int64_t per_strip = std::max<int64_t>(1, target / nstrips);

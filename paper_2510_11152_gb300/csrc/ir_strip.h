@@ -1,5 +1,5 @@
-// ir_strip.h -- the float64 refinement residual of the mixed-precision solve for 2D cell-centred
-// levels with a constant diffusivity (ir_strip.cu).
+// ir_strip.h -- the float64 refinement residual of the mixed-precision solve with a constant
+// diffusivity (ir_strip.cu): 2D cell-centred levels and 3D levels (cells or faces).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -7,7 +7,8 @@
 
 namespace fasmg {
 
-// True if the strip kernel handles the level (2D, cell-centred, constant kappa, nx a multiple of 128).
+// True if the strip kernels handle the level: constant kappa, nx a multiple of 128; 2D cell-centred,
+// or 3D (cells or faces) with ny a multiple of 8.
 bool ir_strip_supported(const LevelDesc<double>& L);
 
 // r32 = (float)(b - A u) and per-block partials of sum (s r32)^2 (s = *nsp, or 1) into

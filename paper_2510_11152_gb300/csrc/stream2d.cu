@@ -366,6 +366,13 @@ __device__ __forceinline__ void post_body(Ring<UPD>& R, const StripGeo& g, int y
   for (int k = 0; k < kPF; ++k)
     prefetch_row<FAST, UPD>(R, k, uin, f, true, ystart + k, ny, g, nx, u64, ystart + k - LW);
   const int nxc = nx >> 1;
+  // coarse values of the next row pair, loaded one pair ahead of their use (rows y-1, y with y odd)
+  auto load_uc = [&](int yy) {
+    return (yy <= yend && yy >= 1 && yy < ny && g.lane_in)
+               ? *reinterpret_cast<const float2*>(uc + (int64_t)(yy >> 1) * nxc + (g.xl >> 1))
+               : make_float2(0.f, 0.f);
+  };
+  float2 cvn = load_uc(ystart + 1);  // ystart is even
   for (int yb = ystart; yb <= yend; yb += kWin) {
 #pragma unroll
     for (int it = 0; it < kWin; ++it) {
@@ -383,10 +390,14 @@ __device__ __forceinline__ void post_body(Ring<UPD>& R, const StripGeo& g, int y
       const int yw = y - LW;
       const bool wr = yw >= g.y0 && yw < g.y1 && g.lane_out;
       // coarse-grid correction of the row pair (y-1, y)
+      float2 cv = make_float2(0.f, 0.f);
+      if ((it & 1) == 1) {
+        cv = cvn;
+        cvn = load_uc(y + 2);
+      }
       if ((it & 1) == 1 && (FAST || (y < ny && y >= 1 && g.lane_in))) {
         float4& lo = U[(it - 1) & M];
         float4& hi = U[it];
-        const float2 cv = *reinterpret_cast<const float2*>(uc + (int64_t)(y >> 1) * nxc + (g.xl >> 1));
         const float2 ru = avg_pair(lo, hi);
         const float d0 = cv.x - ru.x, d1 = cv.y - ru.y;
         lo.x += d0;

@@ -25,23 +25,27 @@ namespace {
 
 constexpr int kIrWarps = 8;
 constexpr int kIrThreads = 32 * kIrWarps;
-constexpr int kIrCols = 128;  // columns per strip (4 per lane)
+constexpr int kIrCols = 128;  // columns per strip of the 3D kernel (4 per lane); 2D strips are 32 CPL wide
+constexpr int kIrCpl2D = 4;   // cells per lane of the 2D kernel
+constexpr int kIrMinBlocks2D = 2;
 constexpr unsigned kAll = 0xffffffffu;
 constexpr int kExpNone = 1 << 20;  // neutral bounds of an absent row; -kExpNone marks a bad value
 
-// One row of a lane's four cells (x0 .. x0+3), unpacked, with the strip's outer neighbours on
+// One row of a lane's CPL cells (x0 .. x0+CPL-1), unpacked, with the strip's outer neighbours on
 // lanes 0 and 31.
+template <int CPL>
 struct IrRow {
-  int64_t sig[4];  // signed significands including the implicit bit
-  int E[4];        // biased exponents
-  uint64_t halo;   // lane 0: the cell left of the strip; lane 31: the cell right of it (else 0)
-  int lo, hi;      // warp-wide smallest / largest exponent of the row and its halo
+  int64_t sig[CPL];  // signed significands including the implicit bit
+  int E[CPL];        // biased exponents
+  uint64_t halo;     // lane 0: the cell left of the strip; lane 31: the cell right of it (else 0)
+  int lo, hi;        // warp-wide smallest / largest exponent of the row and its halo
   bool present;
 };
 
 // The same row as loaded from memory (bit patterns), before unpacking.
+template <int CPL>
 struct IrRaw {
-  uint64_t v[4];
+  uint64_t v[CPL];
   uint64_t halo;
 };
 
@@ -65,37 +69,53 @@ __device__ __forceinline__ int64_t align(int64_t sig, int E, int Eref) {
   return (int64_t)((uint64_t)sig << (E - Eref));
 }
 
-__device__ __forceinline__ void load_raw(IrRaw& R, const double* __restrict__ u, int y, int nx, int ny, int x0,
+__device__ __forceinline__ double as_d(uint64_t v) { return __longlong_as_double((long long)v); }
+
+// CPL consecutive float64 values from 16-byte aligned p (CPL = 2 or 4)
+template <int CPL>
+__device__ __forceinline__ void ld_vals(double (&v)[CPL], const double* __restrict__ p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < CPL / 2; ++k) {
+    const double2 t = q[k];
+    v[2 * k] = t.x;
+    v[2 * k + 1] = t.y;
+  }
+}
+
+template <int CPL>
+__device__ __forceinline__ void load_raw(IrRaw<CPL>& R, const double* __restrict__ u, int y, int nx, int ny, int x0,
                                          int lane) {
   R.halo = 0ull;
   if (y >= 0 && y < ny) {
     const int64_t base = (int64_t)y * nx + x0;
-    const double2 a = reinterpret_cast<const double2*>(u + base)[0];
-    const double2 b = reinterpret_cast<const double2*>(u + base)[1];
-    R.v[0] = (uint64_t)__double_as_longlong(a.x);
-    R.v[1] = (uint64_t)__double_as_longlong(a.y);
-    R.v[2] = (uint64_t)__double_as_longlong(b.x);
-    R.v[3] = (uint64_t)__double_as_longlong(b.y);
-    if ((lane == 0 && x0 > 0) || (lane == 31 && x0 + 4 < nx))
-      R.halo = (uint64_t)__double_as_longlong(u[lane == 0 ? base - 1 : base + 4]);
+    double v[CPL];
+    ld_vals<CPL>(v, u + base);
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) R.v[k] = (uint64_t)__double_as_longlong(v[k]);
+    if ((lane == 0 && x0 > 0) || (lane == 31 && x0 + CPL < nx))
+      R.halo = (uint64_t)__double_as_longlong(u[lane == 0 ? base - 1 : base + CPL]);
   } else {
-    R.v[0] = R.v[1] = R.v[2] = R.v[3] = 0ull;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) R.v[k] = 0ull;
   }
 }
 
-__device__ __forceinline__ void unpack_row(IrRow& R, const IrRaw& W, int y, int nx, int ny, int x0, int lane) {
+template <int CPL>
+__device__ __forceinline__ void unpack_row(IrRow<CPL>& R, const IrRaw<CPL>& W, int y, int nx, int ny, int x0,
+                                           int lane) {
   R.present = y >= 0 && y < ny;
   int lo = kExpNone, hi = -kExpNone;
   bool bad = false;
   R.halo = W.halo;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < CPL; ++k) {
     unpack(W.v[k], R.sig[k], R.E[k]);
     lo = min(lo, R.E[k]);
     hi = max(hi, R.E[k]);
     bad = bad || bad_exp(R.E[k]);
   }
-  if ((lane == 0 && x0 > 0) || (lane == 31 && x0 + 4 < nx)) {
+  if ((lane == 0 && x0 > 0) || (lane == 31 && x0 + CPL < nx)) {
     const int Eh = (int)((W.halo >> 52) & 0x7FF);
     lo = min(lo, Eh);
     hi = max(hi, Eh);
@@ -110,60 +130,55 @@ __device__ __forceinline__ void unpack_row(IrRow& R, const IrRaw& W, int y, int 
   R.hi = __reduce_max_sync(kAll, hi);
 }
 
-__device__ __forceinline__ double as_d(uint64_t v) { return __longlong_as_double((long long)v); }
-
-// Loads of the b values of row y (4 per lane).
-__device__ __forceinline__ void load_b(double (&bv)[4], const double* __restrict__ b, int y, int ny, int nx, int x0) {
-  if (y < ny) {
-    const int64_t bb = (int64_t)y * nx + x0;
-    const double2 b01 = reinterpret_cast<const double2*>(b + bb)[0];
-    const double2 b23 = reinterpret_cast<const double2*>(b + bb)[1];
-    bv[0] = b01.x;
-    bv[1] = b01.y;
-    bv[2] = b23.x;
-    bv[3] = b23.y;
-  }
+template <int CPL>
+__device__ __forceinline__ void store_r32(float* p, const float (&o)[CPL]) {
+  if constexpr (CPL == 4)
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  else
+    *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
 }
 
-__global__ void __launch_bounds__(kIrThreads, 2)
+// 2D: one warp per strip of 32 CPL columns, walking a segment of rows.
+template <int CPL, int MINB>
+__global__ void __launch_bounds__(kIrThreads, MINB)
     k_ir_strip(float* __restrict__ r32, const double* __restrict__ u, const double* __restrict__ b, LevelDesc<double> L,
                const float* nsp, double* partials, int seg) {
+  constexpr int COLS = 32 * CPL;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nx = L.nx, ny = L.ny;
-  const int nstrips = nx / kIrCols;
+  const int nstrips = nx / COLS;
   const int nseg = (ny + seg - 1) / seg;
   const int ntasks = nstrips * nseg;
   const float nscale = nsp ? *nsp : 1.f;
   float acc = 0.f;
   for (int task = blockIdx.x * kIrWarps + warp; task < ntasks; task += gridDim.x * kIrWarps) {
     const int sx = task % nstrips, sy = task / nstrips;
-    const int x0 = sx * kIrCols + 4 * lane;
+    const int x0 = sx * COLS + CPL * lane;
     const int y0 = sy * seg, y1 = min(ny, y0 + seg);
-    IrRow P, C, N;
-    IrRaw pend;
-    double bv[4];
-    load_raw(pend, u, y0 - 1, nx, ny, x0, lane);
-    unpack_row(P, pend, y0 - 1, nx, ny, x0, lane);
-    load_raw(pend, u, y0, nx, ny, x0, lane);
-    unpack_row(C, pend, y0, nx, ny, x0, lane);
-    load_raw(pend, u, y0 + 1, nx, ny, x0, lane);
-#pragma unroll 1
+    IrRow<CPL> P, C, N;
+    IrRaw<CPL> pend;
+    load_raw<CPL>(pend, u, y0 - 1, nx, ny, x0, lane);
+    unpack_row<CPL>(P, pend, y0 - 1, nx, ny, x0, lane);
+    load_raw<CPL>(pend, u, y0, nx, ny, x0, lane);
+    unpack_row<CPL>(C, pend, y0, nx, ny, x0, lane);
+    load_raw<CPL>(pend, u, y0 + 1, nx, ny, x0, lane);
     for (int y = y0; y < y1; ++y) {
-      // row y+1 arrives from the loads issued one row earlier; rows y+2 and b of y+1 are requested now
-      unpack_row(N, pend, y + 1, nx, ny, x0, lane);
-      load_raw(pend, u, y + 2, nx, ny, x0, lane);
-      load_b(bv, b, y, ny, nx, x0);
+      // row y+1 arrives from the loads issued one row earlier; row y+2 is requested now
+      unpack_row<CPL>(N, pend, y + 1, nx, ny, x0, lane);
+      load_raw<CPL>(pend, u, y + 2, nx, ny, x0, lane);
       const int64_t bb = (int64_t)y * nx + x0;
-      double r[4];
+      double bv[CPL];
+      ld_vals<CPL>(bv, b + bb);
+      double r[CPL];
       const int Eref = min(C.lo, min(P.lo, N.lo));
       const int Etop = max(C.hi, max(P.hi, N.hi));
       bool exact = Etop - Eref <= kMaxExpSpread;  // the same on every lane
       if (exact) {
-        int64_t Xc[4];
+        int64_t Xc[CPL];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) Xc[k] = align(C.sig[k], C.E[k], Eref);
-        long long wl = __shfl_up_sync(kAll, (long long)Xc[3], 1);
+        for (int k = 0; k < CPL; ++k) Xc[k] = align(C.sig[k], C.E[k], Eref);
+        long long wl = __shfl_up_sync(kAll, (long long)Xc[CPL - 1], 1);
         long long er = __shfl_down_sync(kAll, (long long)Xc[0], 1);
         if (lane == 0 || lane == 31) {
           int64_t hs = 0;
@@ -173,12 +188,12 @@ __global__ void __launch_bounds__(kIrThreads, 2)
           if (lane == 0) wl = hx;
           else er = hx;
         }
-        int64_t S[4];
+        int64_t S[CPL];
         if (y > 0 && y < ny - 1) {  // rows with both vertical neighbours (the same on every lane)
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
+          for (int k = 0; k < CPL; ++k) {
             const int64_t Xw = k ? Xc[k - 1] : (int64_t)wl;
-            const int64_t Xe = k < 3 ? Xc[k + 1] : (int64_t)er;
+            const int64_t Xe = k < CPL - 1 ? Xc[k + 1] : (int64_t)er;
             const int64_t V = align(P.sig[k], P.E[k], Eref) + align(N.sig[k], N.E[k], Eref);
             S[k] = (Xw + Xe) + V - 4 * Xc[k];
           }
@@ -187,16 +202,16 @@ __global__ void __launch_bounds__(kIrThreads, 2)
             const int cls = bclass<2>(0, y, 0, nx, ny, 1);
             S[0] += (4 - (int64_t)L.mt[cls]) * Xc[0];
           }
-          if (x0 + 4 == nx) {
+          if (x0 + CPL == nx) {
             const int cls = bclass<2>(nx - 1, y, 0, nx, ny, 1);
-            S[3] += (4 - (int64_t)L.mt[cls]) * Xc[3];
+            S[CPL - 1] += (4 - (int64_t)L.mt[cls]) * Xc[CPL - 1];
           }
         } else {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
+          for (int k = 0; k < CPL; ++k) {
             const int x = x0 + k;
             const int64_t Xw = k ? Xc[k - 1] : (int64_t)wl;
-            const int64_t Xe = k < 3 ? Xc[k + 1] : (int64_t)er;
+            const int64_t Xe = k < CPL - 1 ? Xc[k + 1] : (int64_t)er;
             const int64_t Xs = P.present ? align(P.sig[k], P.E[k], Eref) : 0;
             const int64_t Xn = N.present ? align(N.sig[k], N.E[k], Eref) : 0;
             const int cls = bclass<2>(x, y, 0, nx, ny, 1);
@@ -206,19 +221,19 @@ __global__ void __launch_bounds__(kIrThreads, 2)
         // |S| < 2^53 on every lane (smooth fields): the conversion needs no rounding step
         bool small = true;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < CPL; ++k)
           small = small && (uint64_t)(S[k] + ((1ll << 53) - 1)) < (1ull << 54) - 1ull;
         bool ok = true;
         if (__all_sync(kAll, small)) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
+          for (int k = 0; k < CPL; ++k) {
             double Sd;
             ok = fixed_to_f64_small(S[k], Eref, &Sd) && ok;
             r[k] = fma(L.c, Sd, fma(-L.alpha, as_d(repack(C.sig[k], C.E[k])), bv[k]));
           }
         } else {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
+          for (int k = 0; k < CPL; ++k) {
             double Sd;
             ok = fixed_to_f64(S[k], Eref, &Sd) && ok;
             r[k] = fma(L.c, Sd, fma(-L.alpha, as_d(repack(C.sig[k], C.E[k])), bv[k]));
@@ -227,19 +242,19 @@ __global__ void __launch_bounds__(kIrThreads, 2)
         exact = !__any_sync(kAll, !ok);
       }
       if (!exact) {  // the float64 point equation, as in residual_point, from the values in memory
-        IrRaw rp, rc, rn;
-        load_raw(rp, u, y - 1, nx, ny, x0, lane);
-        load_raw(rc, u, y, nx, ny, x0, lane);
-        load_raw(rn, u, y + 1, nx, ny, x0, lane);
-        double wv = as_d((uint64_t)__shfl_up_sync(kAll, (long long)rc.v[3], 1));
+        IrRaw<CPL> rp, rc, rn;
+        load_raw<CPL>(rp, u, y - 1, nx, ny, x0, lane);
+        load_raw<CPL>(rc, u, y, nx, ny, x0, lane);
+        load_raw<CPL>(rn, u, y + 1, nx, ny, x0, lane);
+        double wv = as_d((uint64_t)__shfl_up_sync(kAll, (long long)rc.v[CPL - 1], 1));
         double ev = as_d((uint64_t)__shfl_down_sync(kAll, (long long)rc.v[0], 1));
         if (lane == 0) wv = as_d(rc.halo);
         if (lane == 31) ev = as_d(rc.halo);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < CPL; ++k) {
           const int x = x0 + k;
           const double w = x > 0 ? (k ? as_d(rc.v[k - 1]) : wv) : 0.0;
-          const double e = x < nx - 1 ? (k < 3 ? as_d(rc.v[k + 1]) : ev) : 0.0;
+          const double e = x < nx - 1 ? (k < CPL - 1 ? as_d(rc.v[k + 1]) : ev) : 0.0;
           const double s = y > 0 ? as_d(rp.v[k]) : 0.0;
           const double n = y < ny - 1 ? as_d(rn.v[k]) : 0.0;
           const double nb = (w + e) + (s + n);
@@ -247,26 +262,23 @@ __global__ void __launch_bounds__(kIrThreads, 2)
           r[k] = fma(L.c, nb, fma(-L.d[cls], as_d(rc.v[k]), bv[k]));
         }
       }
-      float4 o;
-      const bool nrm = f32_normal_range(r[0]) && f32_normal_range(r[1]) && f32_normal_range(r[2]) &&
-                       f32_normal_range(r[3]);
+      float o[CPL];
+      bool nrm = true;
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) nrm = nrm && f32_normal_range(r[k]);
       if (__all_sync(kAll, nrm)) {
-        o.x = f64_to_f32_rn_normal(r[0]);
-        o.y = f64_to_f32_rn_normal(r[1]);
-        o.z = f64_to_f32_rn_normal(r[2]);
-        o.w = f64_to_f32_rn_normal(r[3]);
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) o[k] = f64_to_f32_rn_normal(r[k]);
       } else {
-        o.x = f64_to_f32_rn_bits(r[0]);
-        o.y = f64_to_f32_rn_bits(r[1]);
-        o.z = f64_to_f32_rn_bits(r[2]);
-        o.w = f64_to_f32_rn_bits(r[3]);
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) o[k] = f64_to_f32_rn_bits(r[k]);
       }
-      *reinterpret_cast<float4*>(r32 + bb) = o;
-      const float s0 = o.x * nscale, s1 = o.y * nscale, s2 = o.z * nscale, s3 = o.w * nscale;
-      acc = fmaf(s0, s0, acc);
-      acc = fmaf(s1, s1, acc);
-      acc = fmaf(s2, s2, acc);
-      acc = fmaf(s3, s3, acc);
+      store_r32<CPL>(r32 + bb, o);
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) {
+        const float sk = o[k] * nscale;
+        acc = fmaf(sk, sk, acc);
+      }
       P = C;
       C = N;
     }
@@ -510,13 +522,14 @@ cudaError_t launch_ir_strip(float* r32, const double* u, const double* b, const 
     return cudaGetLastError();
   }
   // segments: about four blocks of eight warps per SM, 16..256 rows each (two halo rows per segment)
+  const int nstrips2 = L.nx / (32 * kIrCpl2D);
   const int64_t target = (int64_t)sm_count * 4 * kIrWarps;
-  const int64_t per_strip = std::max<int64_t>(1, target / nstrips);
+  const int64_t per_strip = std::max<int64_t>(1, target / nstrips2);
   const int seg = (int)std::min<int64_t>(256, std::max<int64_t>(16, (L.ny + per_strip - 1) / per_strip));
-  const int64_t ntasks = (int64_t)nstrips * ((L.ny + seg - 1) / seg);
+  const int64_t ntasks = (int64_t)nstrips2 * ((L.ny + seg - 1) / seg);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(max_blocks, (ntasks + kIrWarps - 1) / kIrWarps));
   *nblocks = blocks;
-  k_ir_strip<<<blocks, kIrThreads, 0, stream>>>(r32, u, b, L, nsp, partials, seg);
+  k_ir_strip<kIrCpl2D, kIrMinBlocks2D><<<blocks, kIrThreads, 0, stream>>>(r32, u, b, L, nsp, partials, seg);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,8 @@ struct NsGrid {
   int lx, ly;
   int64_t cells;
   double h;
+  double hinv;  // 1/h, exact when hpow2
+  bool hpow2;   // h is a power of two
 };
 
 __device__ __forceinline__ int64_t ns_tid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
@@ -82,17 +84,26 @@ __device__ __forceinline__ double tangential_value(const double* __restrict__ ph
 
 // Third-order WENO of Jiang and Shu for a derivative from three consecutive first differences, the
 // upwind one first: the two candidate slopes (3b - a)/2 and (b + c)/2 weighted by the ideal weights
-// 1/3 and 2/3 over the square of eps + their smoothness (b - a)^2, (c - b)^2.
+// 1/3 and 2/3 over the square of eps + their smoothness (b - a)^2, (c - b)^2. With the weights
+// alpha_k = d_k / q_k^2 brought to the common denominator 3 q0^2 q1^2 the combination is
+// (q1^2 p0 + 2 q0^2 p1) / (q1^2 + 2 q0^2): one division instead of three (float64 division is a long
+// sequence on the FP64 pipe).
 __device__ __forceinline__ double weno3(double a, double b, double c) {
   const double p0 = 0.5 * (3.0 * b - a);
   const double p1 = 0.5 * (b + c);
   const double b0 = (b - a) * (b - a);
   const double b1 = (c - b) * (c - b);
   const double q0 = kWenoEps + b0, q1 = kWenoEps + b1;
-  const double a0 = (1.0 / 3.0) / (q0 * q0);
-  const double a1 = (2.0 / 3.0) / (q1 * q1);
-  return (a0 * p0 + a1 * p1) / (a0 + a1);
+  const double w0 = q1 * q1, w1 = 2.0 * (q0 * q0);
+  return (w0 * p0 + w1 * p1) / (w0 + w1);
 }
+
+// x / h, as a multiplication by the exact reciprocal when h is a power of two (then bitwise equal)
+struct InvH {
+  double h, inv;
+  bool pow2;
+  __device__ __forceinline__ double operator()(double x) const { return pow2 ? x * inv : x / h; }
+};
 
 // f_C = c^n - dt (u^n . grad c^n)_WENO3 - dt (p^n_{s+1} - p^n_s)/h + dt F (F: body force at t^{n+1},
 // optional), plus the lid's tangential wall velocity folded into the cells next to the top wall
@@ -105,6 +116,7 @@ __global__ void k_ns_source(double* __restrict__ f, const double* __restrict__ U
   const double* vel[3] = {U, V, W};
   const double* __restrict__ phi = vel[C];
   const double h = G.h;
+  const InvH dh{G.h, G.hinv, G.hpow2};
   for (int64_t idx = ns_tid(); idx < G.cells; idx += ns_stride()) {
     int k[3];
     ns_coords(G, idx, k);
@@ -126,7 +138,7 @@ __global__ void k_ns_source(double* __restrict__ f, const double* __restrict__ U
 #pragma unroll
         for (int s = -2; s <= 2; ++s) v[s + 2] = tangential_value(phi, line, st, G.n[a], k[a] + s, 0.0, g_hi);
       }
-      const double d1 = (v[1] - v[0]) / h, d2 = (v[2] - v[1]) / h, d3 = (v[3] - v[2]) / h, d4 = (v[4] - v[3]) / h;
+      const double d1 = dh(v[1] - v[0]), d2 = dh(v[2] - v[1]), d3 = dh(v[3] - v[2]), d4 = dh(v[4] - v[3]);
       const double dm = weno3(d1, d2, d3);
       const double dp = weno3(d4, d3, d2);
       double adv;
@@ -144,7 +156,7 @@ __global__ void k_ns_source(double* __restrict__ f, const double* __restrict__ U
       }
       conv = conv + (adv > 0.0 ? adv * dm : adv * dp);
     }
-    const double gp = (P[idx + G.st[C]] - P[idx]) / h;
+    const double gp = dh(P[idx + G.st[C]] - P[idx]);
     double v = phi[idx] - dt * conv - dt * gp;
     if (F) v = v + dt * F[idx];
     if (C != DIM - 1 && k[DIM - 1] == G.n[DIM - 1] - 1) v = v + 2.0 * beta * lid_c / (h * h);
@@ -170,6 +182,7 @@ __global__ void k_ns_source2(double* __restrict__ f, const double* __restrict__ 
   const double* __restrict__ cc = cur[C];
   const double* __restrict__ co = old[C];
   const double h = G.h;
+  const InvH dh{G.h, G.hinv, G.hpow2};
   for (int64_t idx = ns_tid(); idx < G.cells; idx += ns_stride()) {
     int k[3];
     ns_coords(G, idx, k);
@@ -215,7 +228,7 @@ __global__ void k_ns_source2(double* __restrict__ f, const double* __restrict__ 
         const double hi = k[a] < n - 1 ? cc[idx + st] : -c0;
         lap += (hi - c0) - (c0 - lo);
       }
-      const double d1 = (v[1] - v[0]) / h, d2 = (v[2] - v[1]) / h, d3 = (v[3] - v[2]) / h, d4 = (v[4] - v[3]) / h;
+      const double d1 = dh(v[1] - v[0]), d2 = dh(v[2] - v[1]), d3 = dh(v[3] - v[2]), d4 = dh(v[4] - v[3]);
       const double dm = weno3(d1, d2, d3);
       const double dp = weno3(d4, d3, d2);
       double adv;
@@ -233,8 +246,8 @@ __global__ void k_ns_source2(double* __restrict__ f, const double* __restrict__ 
       }
       conv = conv + (adv > 0.0 ? adv * dm : adv * dp);
     }
-    const double gp = (P[idx + G.st[C]] - P[idx]) / h;
-    double v = c0 - dt * conv + beta * (lap / (h * h)) - dt * gp;
+    const double gp = dh(P[idx + G.st[C]] - P[idx]);
+    double v = c0 - dt * conv + beta * dh(dh(lap)) - dt * gp;
     if (F) v = v + dt * F[idx];
     if (C != DIM - 1 && k[DIM - 1] == G.n[DIM - 1] - 1) v = v + 2.0 * (2.0 * beta * lid_c / (h * h));
     f[idx] = v;
@@ -246,6 +259,7 @@ template <int DIM>
 __global__ void k_ns_neg_div(double* __restrict__ rhs, const double* __restrict__ U, const double* __restrict__ V,
                              const double* __restrict__ W, NsGrid G) {
   const double* vel[3] = {U, V, W};
+  const InvH dh{G.h, G.hinv, G.hpow2};
   for (int64_t idx = ns_tid(); idx < G.cells; idx += ns_stride()) {
     int k[3];
     ns_coords(G, idx, k);
@@ -254,7 +268,7 @@ __global__ void k_ns_neg_div(double* __restrict__ rhs, const double* __restrict_
     for (int a = 0; a < DIM; ++a) {
       const double* __restrict__ A = vel[a];
       const double lo = k[a] > 0 ? A[idx - G.st[a]] : 0.0;
-      div = div + (A[idx] - lo) / G.h;
+      div = div + dh(A[idx] - lo);
     }
     rhs[idx] = -div;
   }
@@ -269,13 +283,14 @@ __global__ void k_ns_project(double* Uo, double* Vo, double* Wo, const double* U
                              double dt) {
   double* out[3] = {Uo, Vo, Wo};
   const double* in[3] = {Un, Vn, Wn};
+  const InvH dh{G.h, G.hinv, G.hpow2};
   for (int64_t idx = ns_tid(); idx < G.cells; idx += ns_stride()) {
     int k[3];
     ns_coords(G, idx, k);
     const double pc = Pn[idx];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      const double gp = k[a] < G.n[a] - 1 ? (Pn[idx + G.st[a]] - pc) / G.h : 0.0;
+      const double gp = k[a] < G.n[a] - 1 ? dh(Pn[idx + G.st[a]] - pc) : 0.0;
       out[a][idx] = in[a][idx] - dt * gp;
     }
     Po[idx] = Po[idx] + pc;
@@ -287,6 +302,7 @@ template <int DIM>
 __global__ void k_ns_div_max(const double* __restrict__ U, const double* __restrict__ V,
                              const double* __restrict__ W, NsGrid G, double* partials) {
   const double* vel[3] = {U, V, W};
+  const InvH dh{G.h, G.hinv, G.hpow2};
   double m = 0.0;
   for (int64_t idx = ns_tid(); idx < G.cells; idx += ns_stride()) {
     int k[3];
@@ -296,7 +312,7 @@ __global__ void k_ns_div_max(const double* __restrict__ U, const double* __restr
     for (int a = 0; a < DIM; ++a) {
       const double* __restrict__ A = vel[a];
       const double lo = k[a] > 0 ? A[idx - G.st[a]] : 0.0;
-      div = div + (A[idx] - lo) / G.h;
+      div = div + dh(A[idx] - lo);
     }
     m = fmax(m, fabs(div));
   }
@@ -428,6 +444,12 @@ fas_status ns_create(int dim, const int n[3], double h, double Re, double dt, in
   while ((1 << G.ly) < G.n[1]) ++G.ly;
   G.cells = G.st[2] * G.n[2];
   G.h = h;
+  {
+    int e = 0;
+    const double m = std::frexp(h, &e);  // h = m 2^e, m in [0.5, 1)
+    G.hpow2 = m == 0.5;
+    G.hinv = 1.0 / h;
+  }
   auto bail = [&](fas_status s) {
     ns_destroy(c);
     return s;

@@ -6,6 +6,8 @@
 // No pointer here is declared __restrict__ or read through the non-coherent path: the single-CTA
 // kernel writes a level in one step and reads it in the next, separated only by __syncthreads.
 #pragma once
+#include <type_traits>
+
 #include "bits64.cuh"
 #include "common.cuh"
 
@@ -201,11 +203,15 @@ __device__ __forceinline__ void prolong_face_range(T* u, const T* uc, const T* u
     const int nf3[3] = {nxf, nyf, nzf};
     const int nc3[3] = {nxc, nyc, nzc};
     if (f3[FAX] == nf3[FAX] - 1) continue;
+    // per axis two coarse positions and weights (weight 0: the term is absent)
     int cp[3][2];
     T cw[3][2];
-    int cnt[3] = {1, 1, 1};
-    cp[2][0] = 0;
-    cw[2][0] = T(1);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      cp[ax][0] = cp[ax][1] = 0;
+      cw[ax][0] = ax < DIM ? T(0) : T(1);
+      cw[ax][1] = T(0);
+    }
 #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) {
       const int fi = f3[ax], C = fi >> 1;
@@ -217,12 +223,10 @@ __device__ __forceinline__ void prolong_face_range(T* u, const T* uc, const T* u
           // coarse slots C - 1 and C, each with weight 1/2 unless it is a wall (slot -1, or the
           // coarse wall slot nc - 1): a wall face contributes 0
           const bool lo = C >= 1, hi = C < nc3[ax] - 1;
-          cp[ax][0] = hi ? C : C - 1;
-          cw[ax][0] = (hi || lo) ? T(0.5) : T(0);
-          cp[ax][1] = C - 1;
-          cw[ax][1] = T(0.5);
-          cnt[ax] = (hi && lo) ? 2 : 1;
-          if (!hi && !lo) cp[ax][0] = 0;
+          cp[ax][0] = hi ? C : 0;
+          cw[ax][0] = hi ? T(0.5) : T(0);
+          cp[ax][1] = lo ? C - 1 : 0;
+          cw[ax][1] = lo ? T(0.5) : T(0);
         }
       } else {
         const int nb = (fi & 1) ? C + 1 : C - 1;
@@ -231,16 +235,21 @@ __device__ __forceinline__ void prolong_face_range(T* u, const T* uc, const T* u
         cw[ax][0] = T(0.75);
         cp[ax][1] = ghost ? C : nb;
         cw[ax][1] = ghost ? T(-0.25) : T(0.25);
-        cnt[ax] = 2;
       }
     }
     T acc = T(0);
-    for (int a0 = 0; a0 < cnt[0]; ++a0)
-      for (int a1 = 0; a1 < cnt[1]; ++a1)
-        for (int a2 = 0; a2 < cnt[2]; ++a2) {
-          const int64_t I = ((int64_t)cp[2][a2] * nyc + cp[1][a1]) * nxc + cp[0][a0];
-          const T cv = uc0 ? uc[I] - uc0[I] : uc[I];
-          acc += (cw[0][a0] * cw[1][a1] * cw[2][a2]) * cv;
+#pragma unroll
+    for (int a0 = 0; a0 < 2; ++a0)
+#pragma unroll
+      for (int a1 = 0; a1 < 2; ++a1)
+#pragma unroll
+        for (int a2 = 0; a2 < (DIM == 3 ? 2 : 1); ++a2) {
+          const T w = cw[0][a0] * cw[1][a1] * cw[2][a2];
+          if (w != T(0)) {
+            const int64_t I = ((int64_t)cp[2][a2] * nyc + cp[1][a1]) * nxc + cp[0][a0];
+            const T cv = uc0 ? uc[I] - uc0[I] : uc[I];
+            acc += w * cv;
+          }
         }
     u[idx] += acc;
   }
@@ -257,6 +266,88 @@ __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * block
 template <typename T, int DIM>
 __global__ void k_smooth_colour(T* u, const T* f, LevelDesc<T> L, int colour) {
   smooth_colour_range<T, DIM>(u, f, L, colour, gtid(), gstride());
+}
+
+// One colour phase with a thread per group of 4 consecutive cells of a row (nx a multiple of 4,
+// constant kappa): the group is read and written as 16-byte vectors and its 2 cells of the colour
+// are updated with point_update's expression (the other 2, of the other colour, are written back
+// unchanged; no thread writes them in this phase).
+template <typename T>
+struct Quad;
+template <>
+struct Quad<float> {
+  float v[4];
+  __device__ __forceinline__ void ld(const float* p) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+  }
+  __device__ __forceinline__ void st(float* p) const {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct Quad<double> {
+  double v[4];
+  __device__ __forceinline__ void ld(const double* p) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+  __device__ __forceinline__ void st(double* p) const {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+template <typename T, int DIM>
+__global__ void k_smooth_colour4(T* u, const T* f, LevelDesc<T> L, int colour) {
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  const int gpr = nx >> 2;  // groups per row
+  const int64_t ngroups = (int64_t)gpr * ny * nz;
+  for (int64_t g = gtid(); g < ngroups; g += gstride()) {
+    const int x0 = (int)(g % gpr) << 2;
+    const int64_t rest = g / gpr;
+    const int j = (int)(rest % ny);
+    const int l = (int)(rest / ny);
+    const int64_t idx = ((int64_t)l * ny + j) * nx + x0;
+    Quad<T> c, s4, n4, b4, t4, f4;
+    c.ld(u + idx);
+    f4.ld(f + idx);
+    const T wedge = x0 > 0 ? u[idx - 1] : T(0);
+    const T eedge = x0 + 4 < nx ? u[idx + 4] : T(0);
+    if (j > 0) s4.ld(u + idx - sy);
+    if (j < ny - 1) n4.ld(u + idx + sy);
+    if (DIM == 3) {
+      if (l > 0) b4.ld(u + idx - sz);
+      if (l < nz - 1) t4.ld(u + idx + sz);
+    }
+    // cell x has the colour when (x + j + l + DIM + colour) is even; the same along a row
+    auto upd = [&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      const int i = x0 + k;
+      if (L.fax >= 0 && frozen(L, i, j, l)) return;
+      const T w = i > 0 ? (k > 0 ? c.v[k > 0 ? k - 1 : 0] : wedge) : T(0);
+      const T e = i < nx - 1 ? (k < 3 ? c.v[k < 3 ? k + 1 : 3] : eedge) : T(0);
+      const T sv = j > 0 ? s4.v[k] : T(0);
+      const T nv = j < ny - 1 ? n4.v[k] : T(0);
+      T acc = (w + e) + (sv + nv);
+      if (DIM == 3) {
+        const T bo = l > 0 ? b4.v[k] : T(0);
+        const T to = l < nz - 1 ? t4.v[k] : T(0);
+        acc = acc + (bo + to);
+      }
+      const int cls = bclass<DIM>(i, j, l, nx, ny, nz);
+      c.v[k] = fma(L.a[cls], acc, L.b[cls] * f4.v[k]);
+    };
+    if (((x0 + j + l + DIM + colour) & 1) == 0) {
+      upd(std::integral_constant<int, 0>());
+      upd(std::integral_constant<int, 2>());
+    } else {
+      upd(std::integral_constant<int, 1>());
+      upd(std::integral_constant<int, 3>());
+    }
+    c.st(u + idx);
+  }
 }
 
 // r (nullable) = f - A u; per-block partial of sum (s r)^2 into partials[blockIdx.x], s = *nsp (or 1).
@@ -566,6 +657,17 @@ __device__ __forceinline__ void restrict_resid_face_range(T* uc, T* uc0, T* fc, 
     uc0[I] = v;
     fc[I] = wall ? T(0) : face_avg_of<T, DIM, FAX>(resid, ic, jc, lc, nxf, nyf);
   }
+}
+
+// Grid-wide restriction with the residual evaluated per child on the fly (never stored):
+// uc = uc0 = R(u), fc = R(f - A u); the same per-point arithmetic and association as k_residual
+// followed by k_restrict / k_restrict_face, so the results are identical.
+template <typename T, int DIM, int FAX>
+__global__ void k_restrict_resid(T* uc, T* uc0, T* fc, const T* u, const T* f, LevelDesc<T> L) {
+  if constexpr (FAX < 0)
+    restrict_resid_range<T, DIM>(uc, uc0, fc, u, f, L, gtid(), gstride());
+  else
+    restrict_resid_face_range<T, DIM, FAX>(uc, uc0, fc, u, f, L, gtid(), gstride());
 }
 
 // FAX = -1: cell-centred levels; 0..2: face grids normal to that index axis.

@@ -442,6 +442,20 @@ void launch_prolong(fas_ctx* c, int64_t n, T* u, const T* uc, const T* uc0, int 
 template <typename T, int DIM>
 void launch_smooth(fas_ctx* c, const LevelDesc<T>& L, int level, T* u, const T* f, int sweeps) {
   const int64_t half = (int64_t)(L.nx / 2) * L.ny * L.nz;
+  if (!L.varkappa && L.nx % 4 == 0) {  // 16-byte groups of 4 cells
+    const int g4 = grid_for(c, half / 2);
+    for (int s = 0; s < sweeps; ++s) {
+      {
+        Prof pr(c, FAS_K_SMOOTH, level, (double)half);
+        k_smooth_colour4<T, DIM><<<g4, kBlock, 0, c->stream>>>(u, f, L, 1);
+      }
+      {
+        Prof pr(c, FAS_K_SMOOTH, level, (double)half);
+        k_smooth_colour4<T, DIM><<<g4, kBlock, 0, c->stream>>>(u, f, L, 0);
+      }
+    }
+    return;
+  }
   const int g = grid_for(c, half);
   for (int s = 0; s < sweeps; ++s) {
     {
@@ -504,14 +518,14 @@ fas_status vcycle_basic_from(fas_ctx* c, Hier<T>& H, int lfrom, T* utop, const T
     const T* f = l == lfrom ? ftop : H.f[l];
     launch_smooth<T, DIM>(c, L, l, u, f, p.nu1);
     const int64_t n = (int64_t)L.nx * L.ny * L.nz;
-    {
-      Prof pr(c, FAS_K_RESIDUAL, l, (double)n);
-      k_residual<T, DIM><<<grid_for(c, n), kBlock, 0, c->stream>>>(H.r[l], u, f, L, nullptr, nullptr);
-    }
     const int64_t nc = n >> DIM;
-    {
+    {  // residual and its restriction in one pass (the residual is not stored)
       Prof pr(c, FAS_K_RESTRICT, l, (double)n);
-      launch_restrict<T, DIM>(c, nc, H.u[l + 1], H.u0[l + 1], H.f[l + 1], u, H.r[l], L.nx, L.ny, L.nz);
+      with_fax(c, [&](auto tag) {
+        constexpr int FAX = decltype(tag)::value;
+        k_restrict_resid<T, DIM, FAX><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.u[l + 1], H.u0[l + 1],
+                                                                                 H.f[l + 1], u, f, L);
+      });
     }
     {
       Prof pr(c, FAS_K_TAU, l + 1, (double)nc);

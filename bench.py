@@ -45,6 +45,12 @@ def parse():
     ap.add_argument("--inner", type=int, default=0, help="float32 cycles per refinement step (0: tune)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison arm")
+    ap.add_argument("--case", default="heat2d", choices=["heat2d", "heat3d", "ns"],
+                    help="heat2d: the benchmark line; heat3d / ns: one small timed case of the 3D heat or the "
+                         "cavity workload (for kernel profiles), printed as its own JSON line")
+    ap.add_argument("--shape", default="256,512,512", help="--case heat3d: nz,ny,nx (planes of the 512^3 recipe)")
+    ap.add_argument("--ns-n", type=int, default=128, help="--case ns: cells per axis of the 3D cavity")
+    ap.add_argument("--ns-order", type=int, default=1, help="--case ns: projection scheme order")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel from the host instead of one CUDA graph per solve (the same "
                          "kernels; ncu cannot list kernel nodes of graphs with conditional nodes)")
@@ -588,11 +594,57 @@ def run_reference(args, ws, rank):
     print(json.dumps(line))
 
 
+def run_case(args):
+    """One small timed case of the 3D heat or cavity workload (single GPU), e.g. for ncu captures."""
+    import numpy as np
+    import torch
+
+    import paper_2510_11152_gb300 as fas
+    from workloads import heat3d, ns_cavity
+    fas.load()
+    graph = 0 if args.no_graph else 1
+    out = {"case": args.case, "launch": "host loop" if args.no_graph else "one CUDA graph per solve"}
+    if args.case == "heat3d":
+        nz, ny, nx = (int(v) for v in args.shape.split(","))
+        w = heat3d(n=nx)
+        u0 = torch.from_numpy(np.ascontiguousarray(w["u0"][:nz, :ny, :nx])).cuda()
+        ctx = fas.fas_create(fas.make_params((nz, ny, nx), w["h"], alpha=1.0, beta=w["dt"], coarsest=4, precision=1,
+                                             use_graph=graph))
+        u = u0.clone()
+        t0 = time.perf_counter()
+        infos = fas.fas_heat_run(ctx, u, None, w["dt"], args.heat_steps)
+        torch.cuda.synchronize()
+        out.update({"shape": [nz, ny, nx], "steps": args.heat_steps, "ms": (time.perf_counter() - t0) * 1e3,
+                    "cycles": [i.cycles for i in infos]})
+    else:
+        w = ns_cavity(n=args.ns_n, dim=3, nsteps=args.heat_steps)
+        sp = fas.fas_default_params()
+        sp.precision, sp.kmax, sp.coarsest, sp.use_graph = 1, 40, 4, graph
+        pp = fas.fas_default_params()
+        pp.precision, pp.kmax, pp.coarsest, pp.coarse_exact, pp.use_graph = 1, 60, 4, 1, graph
+        ns = fas.ns_create(w["shape"], w["h"], w["Re"], w["dt"], lid=w["lid"], order=args.ns_order, solver=sp,
+                           pressure=pp)
+        flds = {k: torch.zeros(w["shape"], dtype=torch.float64, device="cuda") for k in w["fields"]}
+        t0 = time.perf_counter()
+        cyc = []
+        for _ in range(args.heat_steps):
+            infos, _ = fas.ns_projection_step(ns, flds, want_div=False)
+            cyc.append([i.cycles for i in infos])
+        torch.cuda.synchronize()
+        out.update({"n": args.ns_n, "order": args.ns_order, "steps": args.heat_steps,
+                    "ms": (time.perf_counter() - t0) * 1e3, "cycles_u_v_w_p": cyc})
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.case != "heat2d":
+        if rank == 0:
+            run_case(args)
         return
     run_ours(args, ws, rank, local)
 

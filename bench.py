@@ -190,12 +190,8 @@ def run_ours(args, ws, rank, local):
             dist.barrier()
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        from paper_2510_11152_gb300.shard import max_over_ranks as mor
+        return mor(x, ws, dev)
 
     n = args.n
     w = heat2d_large(n=n, nsteps=args.heat_steps)
@@ -358,7 +354,7 @@ def run_ours(args, ws, rank, local):
         del u0_d, f_d, u_d, u_final
         fas.fas_destroy(ctx)
         torch.cuda.empty_cache()
-        secondary = secondary_workloads(dev, stream)
+        secondary = secondary_workloads(dev, stream, ws, rank)
 
     if rank == 0:
         line = {
@@ -397,10 +393,12 @@ def _event_ms(stream, fn, warmup=1):
     return e0.elapsed_time(e1), out
 
 
-def secondary_workloads(dev, stream):
+def secondary_workloads(dev, stream, ws=1, rank=0):
     """The other workloads of the method, each once after one warm-up run (float64 vs mixed where both
     apply): 3D heat 512^3, the 256^3 lid-driven cavity projection steps, 96 batched Helmholtz solves in
-    one graph launch, the 1024^2 adjoint heat run. Inputs are the seeded recipes of workloads/."""
+    one graph launch, the 1024^2 adjoint heat run. Inputs are the seeded recipes of workloads/. Under
+    several ranks the batched problems are shared out (cell-balanced, no data exchange) and the other
+    workloads run as one replica per rank."""
     import numpy as np
     import torch
 
@@ -485,8 +483,11 @@ def secondary_workloads(dev, stream):
     del zero, ns_res
     torch.cuda.empty_cache()
 
-    # batched: 96 independent 2D Helmholtz problems in one graph launch, mixed precision
-    probs = batched_helmholtz()
+    # batched: 96 independent 2D Helmholtz problems in one graph launch (per rank), mixed precision
+    from paper_2510_11152_gb300.shard import gather_by_index, max_over_ranks, partition, sum_over_ranks
+    probs_all = batched_helmholtz()
+    mine = partition([p["n"] * p["n"] for p in probs_all], ws)[rank]
+    probs = [probs_all[k] for k in mine]
     fs = [torch.from_numpy(batched_problem_rhs(p)).to(dev) for p in probs]
     ctxs = [fas.fas_create(fas.make_params((p["n"], p["n"]), 1.0 / p["n"], alpha=1.0, beta=p["dt"],
                                            kappa_const=p["kappa"], coarsest=4, precision=fas.FAS_MIXED),
@@ -496,14 +497,19 @@ def secondary_workloads(dev, stream):
     def run_b():
         for t in us:
             t.zero_()
-        return fas.fas_solve_batched(ctxs, us, fs, stream=stream)
+        return fas.fas_solve_batched(ctxs, us, fs, stream=stream) if ctxs else []
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
     ms, infos = _event_ms(stream, run_b)
-    work = sum(p["n"] * p["n"] * i.cycles for p, i in zip(probs, infos))
+    ms = max_over_ranks(ms, ws, dev)
+    work = sum_over_ranks(sum(p["n"] * p["n"] * i.cycles for p, i in zip(probs, infos)), ws, dev)
+    conv = gather_by_index({k: bool(i.converged) for k, i in zip(mine, infos)}, ws, len(probs_all))
     out["batched_96"] = {"workload": "96 2D Helmholtz problems, n in 64..2048, kappa U(0.5,2), dt {1e-4,1e-3}, "
-                                     "mixed, tol 1e-10, one graph launch",
+                                     "mixed, tol 1e-10, one graph launch per rank",
                          "ms": ms, "Mcells_vcycles_per_s": work / (ms / 1e3) / 1e6,
-                         "fine_cells": sum(p["n"] * p["n"] for p in probs),
-                         "converged_all": all(i.converged for i in infos)}
+                         "fine_cells": sum(p["n"] * p["n"] for p in probs_all), "ranks": ws,
+                         "converged_all": all(conv)}
     for c in ctxs:
         fas.fas_destroy(c)
     del fs, us, ctxs

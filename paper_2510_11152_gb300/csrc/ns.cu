@@ -138,9 +138,6 @@ __global__ void k_ns_source(double* __restrict__ f, const double* __restrict__ U
 #pragma unroll
         for (int s = -2; s <= 2; ++s) v[s + 2] = tangential_value(phi, line, st, G.n[a], k[a] + s, 0.0, g_hi);
       }
-      const double d1 = dh(v[1] - v[0]), d2 = dh(v[2] - v[1]), d3 = dh(v[3] - v[2]), d4 = dh(v[4] - v[3]);
-      const double dm = weno3(d1, d2, d3);
-      const double dp = weno3(d4, d3, d2);
       double adv;
       if (a == C) {
         adv = phi[idx];
@@ -154,7 +151,13 @@ __global__ void k_ns_source(double* __restrict__ f, const double* __restrict__ U
         const double hi = 0.5 * ((in ? A[idx - sa + sc] : 0.0) + A[idx + sc]);
         adv = 0.5 * (lo + hi);
       }
-      conv = conv + (adv > 0.0 ? adv * dm : adv * dp);
+      // only the upwind WENO3 derivative is used: the left-biased one (differences d1, d2, d3) where
+      // the advecting velocity is positive, the right-biased one (d4, d3, d2) elsewhere
+      const bool up = adv > 0.0;
+      const double d2 = dh(v[2] - v[1]), d3 = dh(v[3] - v[2]);
+      const double dx = up ? dh(v[1] - v[0]) : dh(v[4] - v[3]);
+      const double dd = weno3(dx, up ? d2 : d3, up ? d3 : d2);
+      conv = conv + adv * dd;
     }
     const double gp = dh(P[idx + G.st[C]] - P[idx]);
     double v = phi[idx] - dt * conv - dt * gp;
@@ -228,9 +231,6 @@ __global__ void k_ns_source2(double* __restrict__ f, const double* __restrict__ 
         const double hi = k[a] < n - 1 ? cc[idx + st] : -c0;
         lap += (hi - c0) - (c0 - lo);
       }
-      const double d1 = dh(v[1] - v[0]), d2 = dh(v[2] - v[1]), d3 = dh(v[3] - v[2]), d4 = dh(v[4] - v[3]);
-      const double dm = weno3(d1, d2, d3);
-      const double dp = weno3(d4, d3, d2);
       double adv;
       if (a == C) {
         adv = cbar(idx);
@@ -244,7 +244,13 @@ __global__ void k_ns_source2(double* __restrict__ f, const double* __restrict__ 
         const double hi = 0.5 * ((in ? A(idx - sa + sc) : 0.0) + A(idx + sc));
         adv = 0.5 * (lo + hi);
       }
-      conv = conv + (adv > 0.0 ? adv * dm : adv * dp);
+      // only the upwind WENO3 derivative is used: the left-biased one (differences d1, d2, d3) where
+      // the advecting velocity is positive, the right-biased one (d4, d3, d2) elsewhere
+      const bool up = adv > 0.0;
+      const double d2 = dh(v[2] - v[1]), d3 = dh(v[3] - v[2]);
+      const double dx = up ? dh(v[1] - v[0]) : dh(v[4] - v[3]);
+      const double dd = weno3(dx, up ? d2 : d3, up ? d3 : d2);
+      conv = conv + adv * dd;
     }
     const double gp = dh(P[idx + G.st[C]] - P[idx]);
     double v = c0 - dt * conv + beta * dh(dh(lap)) - dt * gp;

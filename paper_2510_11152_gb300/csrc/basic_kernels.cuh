@@ -571,7 +571,6 @@ struct CoarseArgs {
   const LevelDesc<T>* desc;  // device array, one per level
   T* const* u;               // per-level buffers (entry l0 replaced by utop)
   T* const* f;
-  T* const* r;
   T* const* u0;
   const T* cinv;  // dense inverse of the coarsest operator, or null
   int l0, nlev, nu1, nu2, nuc;

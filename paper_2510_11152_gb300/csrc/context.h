@@ -20,14 +20,13 @@ struct Hier {
   int switch_level = 0;  // levels >= switch_level run inside the single-CTA kernel
   std::vector<LevelDesc<T>> desc;
   LevelDesc<T>* d_desc = nullptr;
-  std::vector<T*> u, f, r, u0;
+  std::vector<T*> u, f, u0;
   std::vector<T*> u2, rc;  // fused path: second u buffer (ping-pong) and R(r) from the finer level
   int nfast = 0;           // levels 0..nfast-1 use the fused kernels
   SmemLayout smem;         // shared-memory layout of the single-CTA kernel (levels >= switch_level)
   size_t smem_bytes = 0;
   T** d_u = nullptr;
   T** d_f = nullptr;
-  T** d_r = nullptr;
   T** d_u0 = nullptr;
   T* cinv = nullptr;
   std::vector<void*> owned;  // every device allocation above

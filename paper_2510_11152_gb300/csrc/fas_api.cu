@@ -158,7 +158,6 @@ void free_hier(Hier<T>& H) {
   H.owned.clear();
   H.u.clear();
   H.f.clear();
-  H.r.clear();
   H.u0.clear();
   H.u2.clear();
   H.rc.clear();
@@ -349,11 +348,9 @@ fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers)
   if (buffers) {
     H.u.assign(c->nlev, nullptr);
     H.f.assign(c->nlev, nullptr);
-    H.r.assign(c->nlev, nullptr);
     H.u0.assign(c->nlev, nullptr);
     for (int l = 0; l < c->nlev; ++l) {
       const int64_t n = c->shape[l].cells();
-      STATUS_TRY(dev_alloc(H, &H.r[l], n));
       if (l > 0 || level0_buffers) {
         STATUS_TRY(dev_alloc(H, &H.u[l], n));
         STATUS_TRY(dev_alloc(H, &H.f[l], n));
@@ -375,15 +372,13 @@ fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers)
       STATUS_TRY(dev_alloc(H, &H.u2[l], c->shape[l].cells()));
       if (l + 1 < H.nfast) STATUS_TRY(dev_alloc(H, &H.rc[l + 1], c->shape[l + 1].cells()));
     }
-    T** arrs[4] = {nullptr, nullptr, nullptr, nullptr};
-    for (int k = 0; k < 4; ++k) STATUS_TRY(dev_alloc(H, &arrs[k], kMaxLevels));
+    T** arrs[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < 3; ++k) STATUS_TRY(dev_alloc(H, &arrs[k], kMaxLevels));
     H.d_u = arrs[0];
     H.d_f = arrs[1];
-    H.d_r = arrs[2];
-    H.d_u0 = arrs[3];
+    H.d_u0 = arrs[2];
     CUDA_TRY(cudaMemcpy(H.d_u, H.u.data(), c->nlev * sizeof(T*), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(H.d_f, H.f.data(), c->nlev * sizeof(T*), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(H.d_r, H.r.data(), c->nlev * sizeof(T*), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(H.d_u0, H.u0.data(), c->nlev * sizeof(T*), cudaMemcpyHostToDevice));
     if (p.coarse_exact) {
       std::vector<double> inv;
@@ -491,7 +486,6 @@ fas_status launch_coarse(fas_ctx* c, Hier<T>& H, int l0, T* utop, const T* ftop)
   A.desc = H.d_desc;
   A.u = H.d_u;
   A.f = H.d_f;
-  A.r = H.d_r;
   A.u0 = H.d_u0;
   A.cinv = H.cinv;
   A.l0 = l0;

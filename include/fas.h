@@ -18,6 +18,10 @@
  *              complete unless stated otherwise). The library owns only the coarse levels and
  *              scratch it allocates in fas_create and frees in fas_destroy.
  *              The *_host entry points take HOST pointers and do the copies themselves.
+ *   Alignment  Every DEVICE field pointer must be 16-byte aligned (the kernels move fields in
+ *              16-byte vectors). cudaMalloc and PyTorch allocations are; a view that starts at an
+ *              odd element is not. A misaligned pointer is rejected with FAS_EINVAL before any
+ *              work is enqueued.
  *   Streams    All device work is enqueued on the cudaStream_t given to fas_create (NULL = the
  *              legacy default stream).
  *   Errors     Every call returns a fas_status; nothing aborts or throws. fas_last_error() gives a
@@ -174,7 +178,8 @@ fas_status fas_autotune(fas_ctx* ctx, double* u_scratch, const double* f, fas_tu
 
 /* --- single operators, for testing each kernel against the oracle ---------------------------- */
 
-/* out = f - A u on level `level` (Sec. 2.2, r = f - L_h p), norm2 (may be NULL) = ||out||_2.
+/* out = f - A u on level `level` (Sec. 2.2, r = f - L_h p), norm2 (may be NULL) = ||out||_2; out
+ * may be NULL when only the norm is wanted.
  * Level 0 fields are the caller's; level > 0 operates on caller fields of that level's size. */
 fas_status fas_residual(fas_ctx* ctx, int level, const double* u, const double* f, double* out,
                         double* norm2);
@@ -261,7 +266,8 @@ fas_status fas_vcycle_small_static(const fas_params* p, double* u, const double*
  * instead of the hardware conversions (no counterpart in the paper): converts a fixed list of special
  * values and, for each of `count` seeded pseudo-random draws, a raw 64-bit pattern, three doubles in
  * and around float32's exponent range (random, exact-tie and tie +- 1 significands) and two floats,
- * and compares each result with the hardware conversion. *mismatches (HOST) receives the number of
+ * and compares each result with the hardware conversion (float64 -> float32 both by the general
+ * routine and, inside float32's normal range, by the shorter one the residual kernels use). *mismatches (HOST) receives the number of
  * results that differ in any bit (two NaNs count as equal). Runs on the current device and stream 0. */
 fas_status fas_selftest_conversions(long long count, unsigned long long seed, long long* mismatches);
 

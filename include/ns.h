@@ -13,7 +13,8 @@
  *            slot s (faces 1..n-1 are the unknowns) and the far wall face, which must be 0 and stays
  *            0, at slot n-1; the near wall face is not stored (it is 0).
  * Fields     fields[8] = { U_new, U_old, V_new, V_old, W_new, W_old, P_new, P_old }, DEVICE pointers
- *            owned by the caller (in 2D the W entries are ignored and may be NULL). These are the
+ *            owned by the caller, each 16-byte aligned (in 2D the W entries are ignored and may be
+ *            NULL). These are the
  *            paper's memory-efficient assignments of the schemes to eight resident fields.
  *            First order (Sec. 4.2): on entry *_old hold u^n and p^n, *_new are work fields; after
  *            the call *_old hold u^{n+1}, p^{n+1}, *_new the intermediate velocity and the pressure

@@ -123,17 +123,18 @@ __device__ __forceinline__ bool fixed_to_f64_small(int64_t S, int E, double* out
 __device__ __forceinline__ float f64_to_f32_rn_normal(double x) {
   const uint64_t B = (uint64_t)__double_as_longlong(x);
   const uint32_t hi = (uint32_t)(B >> 32), lo = (uint32_t)B;
-  // float32 bits before rounding: sign, exponent - 896, top 23 significand bits
-  uint32_t q = (hi & 0x80000000u) | ((((hi >> 20) & 0x7FFu) - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  const uint32_t rem = lo & 0x1FFFFFFFu;
-  q += (rem > 0x10000000u || (rem == 0x10000000u && (q & 1u))) ? 1u : 0u;
-  return __uint_as_float(q);
+  // hi:lo shifted left by 3: bits 31..23 hold the low 9 bits of the float64 exponent E, bits 22..0
+  // the top 23 significand bits. E - 896 lies in 1..254, and its low 8 bits are those of E plus 128.
+  const uint32_t w = __funnelshift_l(lo, hi, 3);
+  const uint32_t q = ((w + 0x40000000u) & 0x7FFFFFFFu) | (hi & 0x80000000u);
+  // round to nearest even on the 29 dropped bits: +1 iff rem > 2^28, or rem == 2^28 and q is odd
+  return __uint_as_float(q + (((lo & 0x1FFFFFFFu) + (w & 1u) + 0x0FFFFFFFu) >> 29));
 }
 
 // True if f64_to_f32_rn_normal applies to x.
 __device__ __forceinline__ bool f32_normal_range(double x) {
-  const uint32_t e = ((uint32_t)((uint64_t)__double_as_longlong(x) >> 52)) & 0x7FFu;
-  return e - 897u <= 1150u - 897u;
+  const uint32_t a = (uint32_t)((uint64_t)__double_as_longlong(x) >> 32) & 0x7FFFFFFFu;
+  return a - (897u << 20) < (254u << 20);
 }
 
 // Largest exponent spread handled exactly: significands < 2^58, at most 6 neighbours plus M <= 9

@@ -1,0 +1,31 @@
+// cp_async.cuh -- per-thread asynchronous global -> shared memory copies (cp.async) for the row rings
+// of the streaming kernels: each thread copies its own chunks of a row into a ring slot, one commit
+// group per row, and waits until at most N newer groups are pending before it reads the slot.
+#pragma once
+
+namespace fasmg {
+
+// 16 bytes, both addresses 16-byte aligned. With valid = false nothing is read (gmem must still be a
+// valid address) and the 16 bytes are zero-filled.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid = true) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int bytes = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes) : "memory");
+}
+
+// 8 bytes, both addresses 8-byte aligned.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+}  // namespace fasmg

@@ -1031,6 +1031,14 @@ fas_status check_ctx(const fas_ctx* c) {
   return FAS_OK;
 }
 
+// A device field pointer: non-null where required, and 16-byte aligned (the kernels move fields in
+// 16-byte vectors; a misaligned vector access would fault).
+fas_status check_field(const void* p, bool required, const char* where) {
+  if (!p) return required ? fail(FAS_EINVAL, std::string(where) + ": null field") : FAS_OK;
+  if (reinterpret_cast<uintptr_t>(p) & 15u) return fail(FAS_EINVAL, std::string(where) + ": field not 16-byte aligned");
+  return FAS_OK;
+}
+
 fas_status check_level(const fas_ctx* c, int level, bool needs_coarser) {
   STATUS_TRY(check_ctx(c));
   if (level < 0 || level >= c->nlev || (needs_coarser && level + 1 >= c->nlev))
@@ -1096,6 +1104,7 @@ static __global__ void k_selftest_conv(long long count, unsigned long long seed,
     for (int q = 0; q < 4; ++q) {
       const double d = __longlong_as_double((long long)pats[q]);
       if (!same_or_both_nan_f(f64_to_f32_rn_bits(d), __double2float_rn(d))) ++nbad;
+      if (f32_normal_range(d) && !same_or_both_nan_f(f64_to_f32_rn_normal(d), __double2float_rn(d))) ++nbad;
     }
     const float fx = __uint_as_float((uint32_t)z);
     const float fy = __uint_as_float((uint32_t)(z2 >> 32) & 0x807FFFFFu);  // float32 subnormals
@@ -1117,6 +1126,7 @@ static __global__ void k_selftest_specials(unsigned long long* bad) {
   for (uint64_t p : dpat) {
     const double d = __longlong_as_double((long long)p);
     if (!same_or_both_nan_f(f64_to_f32_rn_bits(d), __double2float_rn(d))) ++nbad;
+    if (f32_normal_range(d) && !same_or_both_nan_f(f64_to_f32_rn_normal(d), __double2float_rn(d))) ++nbad;
   }
   for (uint32_t p : fpat) {
     const float f = __uint_as_float(p);
@@ -1168,6 +1178,7 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
   if (!(p.tol >= 0.0)) return fail(FAS_EINVAL, "tol must be >= 0");
   if (p.alpha < 0.0 || !(p.beta > 0.0)) return fail(FAS_EINVAL, "alpha must be >= 0 and beta > 0");
   if (!p.kappa && !(p.kappa_const > 0.0)) return fail(FAS_EINVAL, "kappa_const must be positive");
+  STATUS_TRY(check_field(p.kappa, false, "fas_create (kappa)"));
   if (p.precision != FAS_FP64 && p.precision != FAS_MIXED) return fail(FAS_EINVAL, "unknown precision");
   for (int k = 0; k < 2 * p.dim; ++k)
     if (p.bc[k] != FAS_BC_NEUMANN && p.bc[k] != FAS_BC_DIRICHLET) return fail(FAS_EINVAL, "unknown bc kind");
@@ -1265,19 +1276,23 @@ int fas_num_levels(const fas_ctx* c) { return c ? c->nlev : 0; }
 
 fas_status fas_vcycle(fas_ctx* c, double* u, const double* f, fas_info* info) {
   STATUS_TRY(check_ctx(c));
-  if (!u || !f) return fail(FAS_EINVAL, "fas_vcycle: null field");
+  STATUS_TRY(check_field(u, true, "fas_vcycle"));
+  STATUS_TRY(check_field(f, true, "fas_vcycle"));
   return solve_impl(c, u, f, info, 1);
 }
 
 fas_status fas_solve(fas_ctx* c, double* u, const double* f, fas_info* info) {
   STATUS_TRY(check_ctx(c));
-  if (!u || !f) return fail(FAS_EINVAL, "fas_solve: null field");
+  STATUS_TRY(check_field(u, true, "fas_solve"));
+  STATUS_TRY(check_field(f, true, "fas_solve"));
   return solve_impl(c, u, f, info, c->p.kmax);
 }
 
 fas_status fas_heat_run(fas_ctx* c, double* u, const double* fsrc, double dt, int nsteps, fas_info* infos) {
   STATUS_TRY(check_ctx(c));
   if (!u || nsteps < 0) return fail(FAS_EINVAL, "fas_heat_run: bad argument");
+  STATUS_TRY(check_field(u, true, "fas_heat_run"));
+  STATUS_TRY(check_field(fsrc, false, "fas_heat_run"));
   if (c->p.alpha != 1.0 || std::fabs(c->p.beta - dt) > 1e-15 * std::fabs(dt))
     return fail(FAS_EINVAL, "fas_heat_run: context must have alpha = 1 and beta = dt");
   const int64_t n = c->shape[0].cells();
@@ -1319,6 +1334,9 @@ fas_status fas_heat_adjoint(fas_ctx* c, const double* u0, const double* fsrc, do
                             int ckpt_every) {
   STATUS_TRY(check_ctx(c));
   if (!u0 || !dL_duT || nsteps < 1) return fail(FAS_EINVAL, "fas_heat_adjoint: bad argument");
+  for (const void* q : {(const void*)u0, (const void*)fsrc, (const void*)dL_duT, (const void*)uT, (const void*)g_u0,
+                        (const void*)g_f, (const void*)g_kappa})
+    STATUS_TRY(check_field(q, false, "fas_heat_adjoint"));
   if (c->p.alpha != 1.0 || std::fabs(c->p.beta - dt) > 1e-15 * std::fabs(dt))
     return fail(FAS_EINVAL, "fas_heat_adjoint: context must have alpha = 1 and beta = dt");
   if (c->p.location != FAS_CELL) return fail(FAS_EUNSUPPORTED, "fas_heat_adjoint: cell-centred unknowns only");
@@ -1425,6 +1443,8 @@ fas_status fas_solve_batched(fas_ctx* const* ctxs, int count, double* const* u, 
   if (!ctxs || !u || !f || count < 1) return fail(FAS_EINVAL, "fas_solve_batched: bad arguments");
   for (int i = 0; i < count; ++i) {
     if (!ctxs[i] || !u[i] || !f[i]) return fail(FAS_EINVAL, "fas_solve_batched: null context or field");
+    STATUS_TRY(check_field(u[i], true, "fas_solve_batched"));
+    STATUS_TRY(check_field(f[i], true, "fas_solve_batched"));
     for (int k = 0; k < i; ++k)
       if (ctxs[k] == ctxs[i]) return fail(FAS_EINVAL, "fas_solve_batched: a context appears twice");
     if (ctxs[i]->prof) return fail(FAS_EINVAL, "fas_solve_batched: kernel timing is on for a context");
@@ -1477,7 +1497,8 @@ fas_status fas_solve_batched(fas_ctx* const* ctxs, int count, double* const* u, 
 
 fas_status fas_autotune(fas_ctx* c, double* u, const double* f, fas_tune_result* out) {
   STATUS_TRY(check_ctx(c));
-  if (!u || !f) return fail(FAS_EINVAL, "fas_autotune: null field");
+  STATUS_TRY(check_field(u, true, "fas_autotune"));
+  STATUS_TRY(check_field(f, true, "fas_autotune"));
   const TuneKey key{c->p.dim, c->shape[0].nx, c->shape[0].ny, c->shape[0].nz, c->p.precision};
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -1546,6 +1567,9 @@ fas_status fas_autotune(fas_ctx* c, double* u, const double* f, fas_tune_result*
 
 fas_status fas_residual(fas_ctx* c, int level, const double* u, const double* f, double* out, double* norm2) {
   STATUS_TRY(check_level(c, level, false));
+  STATUS_TRY(check_field(u, true, "fas_residual"));
+  STATUS_TRY(check_field(f, true, "fas_residual"));
+  STATUS_TRY(check_field(out, false, "fas_residual"));
   const LevelDesc<double>& L = c->h64.desc[level];
   if (c->p.dim == 2)
     launch_residual<double, 2>(c, L, level, out, u, f, nullptr, c->d_scalar);
@@ -1559,7 +1583,8 @@ fas_status fas_residual(fas_ctx* c, int level, const double* u, const double* f,
 
 fas_status fas_residual_ir(fas_ctx* c, const double* u, const double* f, float* r32, double* norm2) {
   STATUS_TRY(check_ctx(c));
-  if (!u || !f || !r32) return fail(FAS_EINVAL, "fas_residual_ir: null field");
+  for (const void* q : {(const void*)u, (const void*)f, (const void*)r32})
+    STATUS_TRY(check_field(q, true, "fas_residual_ir"));
   const int g = launch_ir_residual(c, r32, u, f, nullptr);
   {
     Prof pr(c, FAS_K_NORM, 0, 0.0);
@@ -1592,6 +1617,8 @@ fas_status fas_selftest_conversions(long long count, unsigned long long seed, lo
 fas_status fas_smooth(fas_ctx* c, int level, double* u, const double* f, int sweeps) {
   STATUS_TRY(check_level(c, level, false));
   if (sweeps < 0) return fail(FAS_EINVAL, "sweeps must be >= 0");
+  STATUS_TRY(check_field(u, true, "fas_smooth"));
+  STATUS_TRY(check_field(f, true, "fas_smooth"));
   const LevelDesc<double>& L = c->h64.desc[level];
   if (c->p.dim == 2)
     launch_smooth<double, 2>(c, L, level, u, f, sweeps);
@@ -1604,6 +1631,8 @@ fas_status fas_smooth(fas_ctx* c, int level, double* u, const double* f, int swe
 
 fas_status fas_restrict(fas_ctx* c, int level, const double* u, double* uc) {
   STATUS_TRY(check_level(c, level, true));
+  STATUS_TRY(check_field(u, true, "fas_restrict"));
+  STATUS_TRY(check_field(uc, true, "fas_restrict"));
   const LevelShape& s = c->shape[level];
   const int64_t nc = s.cells() >> c->p.dim;
   {
@@ -1620,6 +1649,8 @@ fas_status fas_restrict(fas_ctx* c, int level, const double* u, double* uc) {
 
 fas_status fas_prolong_add(fas_ctx* c, int level, double* u, const double* cc) {
   STATUS_TRY(check_level(c, level, true));
+  STATUS_TRY(check_field(u, true, "fas_prolong_add"));
+  STATUS_TRY(check_field(cc, true, "fas_prolong_add"));
   const LevelShape& s = c->shape[level];
   const int64_t nc = s.cells() >> c->p.dim;
   {

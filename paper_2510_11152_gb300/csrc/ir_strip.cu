@@ -5,12 +5,13 @@
 // bottleneck of a refinement step when evaluated as five float64 operations per cell. Here the
 // stencil difference S = sum_nb u_nb - M u (M the diagonal's neighbour count plus boundary
 // multiplicities) is summed exactly in 64-bit integers: each value's significand is unpacked once,
-// aligned to the smallest exponent of the three rows around the output row, and the point equation
+// aligned to the smallest exponent of the rows around the output row, and the point equation
 // becomes r = fma(c, S, fma(-alpha, u, b)) (bits64.cuh). One warp owns a strip of 128 columns (four
-// per lane) and walks a segment of rows keeping three unpacked rows in registers; horizontal
-// neighbours come from the adjacent lanes, the strip's outer neighbours from two extra loads.
-// Rows whose values span more than 2^kMaxExpSpread in magnitude, or hold a zero, subnormal or
-// non-finite value, take the float64 point equation instead (the warp decides per row).
+// per lane) and walks a segment of rows (2D) or planes (3D) keeping the neighbouring ones unpacked in
+// registers; horizontal neighbours come from the adjacent lanes, the strip's outer neighbours from
+// two extra loads. Windows whose values span more than 2^kMaxExpSpread in magnitude, or hold a
+// subnormal or non-finite value (2D: also a zero or values of both signs), take the float64 point
+// equation instead (the warp decides per row).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,23 +32,24 @@ constexpr int kIrMinBlocks2D = 2;
 constexpr unsigned kAll = 0xffffffffu;
 constexpr int kExpNone = 1 << 20;  // neutral bounds of an absent row; -kExpNone marks a bad value
 
-// One row of a lane's CPL cells (x0 .. x0+CPL-1), unpacked, with the strip's outer neighbours on
-// lanes 0 and 31.
-template <int CPL>
-struct IrRow {
-  int64_t sig[CPL];  // signed significands including the implicit bit
-  int E[CPL];        // biased exponents
-  uint64_t halo;     // lane 0: the cell left of the strip; lane 31: the cell right of it (else 0)
-  int lo, hi;        // warp-wide smallest / largest exponent of the row and its halo
-  bool present;
-};
-
 // The same row as loaded from memory (bit patterns), before unpacking.
 template <int CPL>
 struct IrRaw {
   uint64_t v[CPL];
-  uint64_t halo;
+  uint64_t halo;  // lane 0: the cell left of the strip; lane 31: the cell right of it (else 0)
 };
+
+// One row of a lane's CPL cells (x0 .. x0+CPL-1) for the exact path of the 2D kernel: the magnitudes
+// of the significands (implicit bit included) aligned to the row's smallest exponent, and
+// t = fma(-alpha, u, b), the part of the point equation outside the stencil difference.
+template <int CPL>
+struct IrRowM {
+  double t[CPL];
+  uint64_t X[CPL];  // |significand| 2^(E - E_lo)
+  uint64_t hX;      // lanes 0 / 31: the strip's outer neighbour, aligned likewise (0 where absent)
+  int kmin, kmax;   // warp-wide min / max of key = (sign << 11) | E over the row and its halo
+};
+constexpr int kKeyNone = 1 << 20;  // kmin of an absent row (kmax: -1)
 
 __device__ __forceinline__ void unpack(uint64_t raw, int64_t& sig, int& E) {
   E = (int)((raw >> 52) & 0x7FF);
@@ -64,12 +66,16 @@ __device__ __forceinline__ uint64_t repack(int64_t sig, int E) {
 
 __device__ __forceinline__ bool bad_exp(int E) { return (unsigned)(E - 1) >= 2046u; }
 
-// sig 2^(E - Eref) as an integer (0 <= E - Eref <= kMaxExpSpread)
-__device__ __forceinline__ int64_t align(int64_t sig, int E, int Eref) {
-  return (int64_t)((uint64_t)sig << (E - Eref));
-}
-
 __device__ __forceinline__ double as_d(uint64_t v) { return __longlong_as_double((long long)v); }
+
+// |significand| of the float64 with bit pattern v and key (sign << 11) | E, times 2^(E - lo) (the
+// shift is taken mod 32: only rows whose exponents span at most kMaxExpSpread are used).
+__device__ __forceinline__ uint64_t mag_aligned(uint64_t v, int key, int lo) {
+  const uint32_t l = (uint32_t)v;
+  const uint32_t m = ((uint32_t)(v >> 32) & 0xFFFFFu) | 0x100000u;
+  const int sh = ((key & 0x7FF) - lo) & 31;
+  return ((uint64_t)__funnelshift_l(l, m, sh) << 32) | (uint64_t)(l << sh);
+}
 
 // CPL consecutive float64 values from 16-byte aligned p (CPL = 2 or 4)
 template <int CPL>
@@ -101,33 +107,54 @@ __device__ __forceinline__ void load_raw(IrRaw<CPL>& R, const double* __restrict
   }
 }
 
+// b of row y (zeros outside the grid)
 template <int CPL>
-__device__ __forceinline__ void unpack_row(IrRow<CPL>& R, const IrRaw<CPL>& W, int y, int nx, int ny, int x0,
-                                           int lane) {
-  R.present = y >= 0 && y < ny;
-  int lo = kExpNone, hi = -kExpNone;
-  bool bad = false;
-  R.halo = W.halo;
+__device__ __forceinline__ void load_b(double (&v)[CPL], const double* __restrict__ b, int y, int nx, int ny, int x0) {
+  if (y >= 0 && y < ny) {
+    ld_vals<CPL>(v, b + (int64_t)y * nx + x0);
+  } else {
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) v[k] = 0.0;
+  }
+}
+
+template <int CPL>
+__device__ __forceinline__ void unpack_rowM(IrRowM<CPL>& R, const IrRaw<CPL>& W, const double (&bw)[CPL], double alpha,
+                                            bool present, int x0, int nx, int lane) {
+  if (!present) {  // the same on every lane
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+      R.t[k] = 0.0;
+      R.X[k] = 0ull;
+    }
+    R.hX = 0ull;
+    R.kmin = kKeyNone;
+    R.kmax = -1;
+    return;
+  }
+  int key[CPL];
+  int kmin = kKeyNone, kmax = -1;
 #pragma unroll
   for (int k = 0; k < CPL; ++k) {
-    unpack(W.v[k], R.sig[k], R.E[k]);
-    lo = min(lo, R.E[k]);
-    hi = max(hi, R.E[k]);
-    bad = bad || bad_exp(R.E[k]);
+    key[k] = (int)(W.v[k] >> 52);
+    kmin = min(kmin, key[k]);
+    kmax = max(kmax, key[k]);
   }
-  if ((lane == 0 && x0 > 0) || (lane == 31 && x0 + CPL < nx)) {
-    const int Eh = (int)((W.halo >> 52) & 0x7FF);
-    lo = min(lo, Eh);
-    hi = max(hi, Eh);
-    bad = bad || bad_exp(Eh);
+  const bool has_halo = (lane == 0 && x0 > 0) || (lane == 31 && x0 + CPL < nx);
+  const int hkey = (int)(W.halo >> 52);
+  if (has_halo) {
+    kmin = min(kmin, hkey);
+    kmax = max(kmax, hkey);
   }
-  if (!R.present) {
-    lo = kExpNone;
-    hi = -kExpNone;
-    bad = false;
+  R.kmin = __reduce_min_sync(kAll, kmin);
+  R.kmax = __reduce_max_sync(kAll, kmax);
+  const int lo = R.kmin & 0x7FF;
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) {
+    R.t[k] = fma(-alpha, as_d(W.v[k]), bw[k]);
+    R.X[k] = mag_aligned(W.v[k], key[k], lo);
   }
-  R.lo = __reduce_min_sync(kAll, bad ? -kExpNone : lo);
-  R.hi = __reduce_max_sync(kAll, hi);
+  R.hX = has_halo ? mag_aligned(W.halo, hkey, lo) : 0ull;
 }
 
 template <int CPL>
@@ -136,6 +163,143 @@ __device__ __forceinline__ void store_r32(float* p, const float (&o)[CPL]) {
     *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
   else
     *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+}
+
+// One output row y of the 2D kernel. P, C hold rows y-1, y; N receives row y+1 from `pend` (u) and
+// `bnext` (b), which are refilled with row y+2.
+//
+// Exact path (decided per warp row): every value of the three rows (and the strip's outer
+// neighbours) is a normal float64 of the same sign sigma, and their exponents span at most
+// kMaxExpSpread binades. Then S = sum_nb u_nb - M u_c = sigma (sum_nb |u_nb| - M |u_c|) is summed
+// exactly on the significand magnitudes aligned to the smallest exponent Eref of the window
+// (|terms| < 2^58, |S| < 2^61) and rounded once; r = fma(c, S, fma(-alpha, u_c, b)). Otherwise the
+// float64 point equation from the values in memory.
+template <int CPL>
+__device__ __forceinline__ void ir_row(const IrRowM<CPL>& P, const IrRowM<CPL>& C, IrRowM<CPL>& N, IrRaw<CPL>& pend,
+                                       double (&bnext)[CPL], int y, float* __restrict__ r32, const double* __restrict__ u,
+                                       const double* __restrict__ b, const LevelDesc<double>& L, int x0, int lane,
+                                       float nscale, float& acc) {
+  const int nx = L.nx, ny = L.ny;
+  // row y+1 arrives from the loads issued one row earlier; row y+2 is requested now
+  unpack_rowM<CPL>(N, pend, bnext, L.alpha, y + 1 < ny, x0, nx, lane);
+  load_raw<CPL>(pend, u, y + 2, nx, ny, x0, lane);
+  load_b<CPL>(bnext, b, y + 2, nx, ny, x0);
+  const int64_t bb = (int64_t)y * nx + x0;
+  double r[CPL];
+  const int kmin = min(C.kmin, min(P.kmin, N.kmin));
+  const int kmax = max(C.kmax, max(P.kmax, N.kmax));
+  const int Eref = kmin & 0x7FF, Etop = kmax & 0x7FF;
+  // the same on every lane: one sign, normal values, exponent spread
+  bool exact = (kmin ^ kmax) < 0x800 && Eref >= 1 && Etop <= 2046 && Etop - Eref <= kMaxExpSpread;
+  if (exact) {
+    uint64_t xp[CPL], xc[CPL], xn[CPL];
+    uint64_t hx = C.hX;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+      xp[k] = P.X[k];
+      xc[k] = C.X[k];
+      xn[k] = N.X[k];
+    }
+    // rows whose smallest exponent is above Eref: shift them to it (absent rows hold zeros)
+    const int dP = P.kmin < kKeyNone ? (P.kmin & 0x7FF) - Eref : 0;
+    const int dC = (C.kmin & 0x7FF) - Eref;
+    const int dN = N.kmin < kKeyNone ? (N.kmin & 0x7FF) - Eref : 0;
+    if (dP | dC | dN) {
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) {
+        xp[k] <<= dP;
+        xc[k] <<= dC;
+        xn[k] <<= dN;
+      }
+      hx <<= dC;
+    }
+    uint64_t wl = (uint64_t)__shfl_up_sync(kAll, (long long)xc[CPL - 1], 1);
+    uint64_t er = (uint64_t)__shfl_down_sync(kAll, (long long)xc[0], 1);
+    if (lane == 0) wl = hx;
+    if (lane == 31) er = hx;
+    int64_t S[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+      const uint64_t Xw = k ? xc[k - 1] : wl;
+      const uint64_t Xe = k < CPL - 1 ? xc[k + 1] : er;
+      S[k] = (int64_t)((Xw + Xe) + (xp[k] + xn[k])) - (int64_t)(xc[k] << 2);
+    }
+    // boundary cells: absent neighbours are 0 above; the diagonal count is mt, not 4
+    if (y == 0 || y == ny - 1) {
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) {
+        const int cls = bclass<2>(x0 + k, y, 0, nx, ny, 1);
+        S[k] += (4 - (int64_t)L.mt[cls]) * (int64_t)xc[k];
+      }
+    } else {
+      if (x0 == 0) S[0] += (4 - (int64_t)L.mt[bclass<2>(0, y, 0, nx, ny, 1)]) * (int64_t)xc[0];
+      if (x0 + CPL == nx) S[CPL - 1] += (4 - (int64_t)L.mt[bclass<2>(nx - 1, y, 0, nx, ny, 1)]) * (int64_t)xc[CPL - 1];
+    }
+    uint64_t A[CPL];
+    int pw[CPL];
+    bool small = true;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+      A[k] = S[k] < 0 ? (uint64_t)(-S[k]) : (uint64_t)S[k];
+      pw[k] = 63 - __clzll((long long)A[k]);  // -1 for S = 0
+      small = small && pw[k] <= 52;
+    }
+    const uint32_t sgm = (uint32_t)(kmin >> 11) << 31;  // sigma
+    double Sd[CPL];
+    bool ok = true;
+    if (__all_sync(kAll, small)) {
+      // |S| < 2^53: exact; |S| 2^(Eref - 1075) = A 2^(52 - p) with the implicit bit adding one to the
+      // exponent field (Eref + p - 53)
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) {
+        const uint64_t q = A[k] << ((52 - pw[k]) & 63);
+        const uint32_t sg = ((uint32_t)(S[k] < 0) << 31) ^ sgm;
+        const uint32_t hw = ((uint32_t)(q >> 32) + ((uint32_t)(Eref + pw[k] - 53) << 20)) | sg;
+        Sd[k] = A[k] ? __hiloint2double((int)hw, (int)(uint32_t)q) : 0.0;
+        ok = ok && (A[k] == 0 || Eref + pw[k] >= 53);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < CPL; ++k) {
+        ok = fixed_to_f64(S[k], Eref, &Sd[k]) && ok;
+        Sd[k] = as_d((uint64_t)__double_as_longlong(Sd[k]) ^ ((uint64_t)sgm << 32));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) r[k] = fma(L.c, Sd[k], C.t[k]);
+    exact = __all_sync(kAll, ok);
+  }
+  if (!exact) {  // the float64 point equation, as in residual_point, from the values in memory
+    const double* __restrict__ uc = u + bb;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+      const int x = x0 + k;
+      const double w = x > 0 ? uc[k - 1] : 0.0;
+      const double e = x < nx - 1 ? uc[k + 1] : 0.0;
+      const double s = y > 0 ? uc[k - nx] : 0.0;
+      const double n = y < ny - 1 ? uc[k + nx] : 0.0;
+      const double nb = (w + e) + (s + n);
+      const int cls = bclass<2>(x, y, 0, nx, ny, 1);
+      r[k] = fma(L.c, nb, fma(-L.d[cls], uc[k], b[bb + k]));
+    }
+  }
+  float o[CPL];
+  bool nrm = true;
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) nrm = nrm && f32_normal_range(r[k]);
+  if (__all_sync(kAll, nrm)) {
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) o[k] = f64_to_f32_rn_normal(r[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) o[k] = f64_to_f32_rn_bits(r[k]);
+  }
+  store_r32<CPL>(r32 + bb, o);
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) {
+    const float sk = o[k] * nscale;
+    acc = fmaf(sk, sk, acc);
+  }
 }
 
 // 2D: one warp per strip of 32 CPL columns, walking a segment of rows.
@@ -156,131 +320,21 @@ __global__ void __launch_bounds__(kIrThreads, MINB)
     const int sx = task % nstrips, sy = task / nstrips;
     const int x0 = sx * COLS + CPL * lane;
     const int y0 = sy * seg, y1 = min(ny, y0 + seg);
-    IrRow<CPL> P, C, N;
+    IrRowM<CPL> R0, R1, R2;  // rows y-1, y, y+1
     IrRaw<CPL> pend;
+    double bnext[CPL];
     load_raw<CPL>(pend, u, y0 - 1, nx, ny, x0, lane);
-    unpack_row<CPL>(P, pend, y0 - 1, nx, ny, x0, lane);
+    load_b<CPL>(bnext, b, y0 - 1, nx, ny, x0);
+    unpack_rowM<CPL>(R0, pend, bnext, L.alpha, y0 - 1 >= 0, x0, nx, lane);
     load_raw<CPL>(pend, u, y0, nx, ny, x0, lane);
-    unpack_row<CPL>(C, pend, y0, nx, ny, x0, lane);
+    load_b<CPL>(bnext, b, y0, nx, ny, x0);
+    unpack_rowM<CPL>(R1, pend, bnext, L.alpha, true, x0, nx, lane);
     load_raw<CPL>(pend, u, y0 + 1, nx, ny, x0, lane);
+    load_b<CPL>(bnext, b, y0 + 1, nx, ny, x0);
     for (int y = y0; y < y1; ++y) {
-      // row y+1 arrives from the loads issued one row earlier; row y+2 is requested now
-      unpack_row<CPL>(N, pend, y + 1, nx, ny, x0, lane);
-      load_raw<CPL>(pend, u, y + 2, nx, ny, x0, lane);
-      const int64_t bb = (int64_t)y * nx + x0;
-      double bv[CPL];
-      ld_vals<CPL>(bv, b + bb);
-      double r[CPL];
-      const int Eref = min(C.lo, min(P.lo, N.lo));
-      const int Etop = max(C.hi, max(P.hi, N.hi));
-      bool exact = Etop - Eref <= kMaxExpSpread;  // the same on every lane
-      if (exact) {
-        int64_t Xc[CPL];
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) Xc[k] = align(C.sig[k], C.E[k], Eref);
-        long long wl = __shfl_up_sync(kAll, (long long)Xc[CPL - 1], 1);
-        long long er = __shfl_down_sync(kAll, (long long)Xc[0], 1);
-        if (lane == 0 || lane == 31) {
-          int64_t hs = 0;
-          int Eh = 0;
-          unpack(C.halo, hs, Eh);
-          const int64_t hx = C.halo ? align(hs, Eh, Eref) : 0;
-          if (lane == 0) wl = hx;
-          else er = hx;
-        }
-        int64_t S[CPL];
-        if (y > 0 && y < ny - 1) {  // rows with both vertical neighbours (the same on every lane)
-#pragma unroll
-          for (int k = 0; k < CPL; ++k) {
-            const int64_t Xw = k ? Xc[k - 1] : (int64_t)wl;
-            const int64_t Xe = k < CPL - 1 ? Xc[k + 1] : (int64_t)er;
-            const int64_t V = align(P.sig[k], P.E[k], Eref) + align(N.sig[k], N.E[k], Eref);
-            S[k] = (Xw + Xe) + V - 4 * Xc[k];
-          }
-          // the two boundary columns of the grid (absent neighbours already 0)
-          if (x0 == 0) {
-            const int cls = bclass<2>(0, y, 0, nx, ny, 1);
-            S[0] += (4 - (int64_t)L.mt[cls]) * Xc[0];
-          }
-          if (x0 + CPL == nx) {
-            const int cls = bclass<2>(nx - 1, y, 0, nx, ny, 1);
-            S[CPL - 1] += (4 - (int64_t)L.mt[cls]) * Xc[CPL - 1];
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < CPL; ++k) {
-            const int x = x0 + k;
-            const int64_t Xw = k ? Xc[k - 1] : (int64_t)wl;
-            const int64_t Xe = k < CPL - 1 ? Xc[k + 1] : (int64_t)er;
-            const int64_t Xs = P.present ? align(P.sig[k], P.E[k], Eref) : 0;
-            const int64_t Xn = N.present ? align(N.sig[k], N.E[k], Eref) : 0;
-            const int cls = bclass<2>(x, y, 0, nx, ny, 1);
-            S[k] = (Xw + Xe) + (Xs + Xn) - (int64_t)L.mt[cls] * Xc[k];
-          }
-        }
-        // |S| < 2^53 on every lane (smooth fields): the conversion needs no rounding step
-        bool small = true;
-#pragma unroll
-        for (int k = 0; k < CPL; ++k)
-          small = small && (uint64_t)(S[k] + ((1ll << 53) - 1)) < (1ull << 54) - 1ull;
-        bool ok = true;
-        if (__all_sync(kAll, small)) {
-#pragma unroll
-          for (int k = 0; k < CPL; ++k) {
-            double Sd;
-            ok = fixed_to_f64_small(S[k], Eref, &Sd) && ok;
-            r[k] = fma(L.c, Sd, fma(-L.alpha, as_d(repack(C.sig[k], C.E[k])), bv[k]));
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < CPL; ++k) {
-            double Sd;
-            ok = fixed_to_f64(S[k], Eref, &Sd) && ok;
-            r[k] = fma(L.c, Sd, fma(-L.alpha, as_d(repack(C.sig[k], C.E[k])), bv[k]));
-          }
-        }
-        exact = !__any_sync(kAll, !ok);
-      }
-      if (!exact) {  // the float64 point equation, as in residual_point, from the values in memory
-        IrRaw<CPL> rp, rc, rn;
-        load_raw<CPL>(rp, u, y - 1, nx, ny, x0, lane);
-        load_raw<CPL>(rc, u, y, nx, ny, x0, lane);
-        load_raw<CPL>(rn, u, y + 1, nx, ny, x0, lane);
-        double wv = as_d((uint64_t)__shfl_up_sync(kAll, (long long)rc.v[CPL - 1], 1));
-        double ev = as_d((uint64_t)__shfl_down_sync(kAll, (long long)rc.v[0], 1));
-        if (lane == 0) wv = as_d(rc.halo);
-        if (lane == 31) ev = as_d(rc.halo);
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) {
-          const int x = x0 + k;
-          const double w = x > 0 ? (k ? as_d(rc.v[k - 1]) : wv) : 0.0;
-          const double e = x < nx - 1 ? (k < CPL - 1 ? as_d(rc.v[k + 1]) : ev) : 0.0;
-          const double s = y > 0 ? as_d(rp.v[k]) : 0.0;
-          const double n = y < ny - 1 ? as_d(rn.v[k]) : 0.0;
-          const double nb = (w + e) + (s + n);
-          const int cls = bclass<2>(x, y, 0, nx, ny, 1);
-          r[k] = fma(L.c, nb, fma(-L.d[cls], as_d(rc.v[k]), bv[k]));
-        }
-      }
-      float o[CPL];
-      bool nrm = true;
-#pragma unroll
-      for (int k = 0; k < CPL; ++k) nrm = nrm && f32_normal_range(r[k]);
-      if (__all_sync(kAll, nrm)) {
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) o[k] = f64_to_f32_rn_normal(r[k]);
-      } else {
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) o[k] = f64_to_f32_rn_bits(r[k]);
-      }
-      store_r32<CPL>(r32 + bb, o);
-#pragma unroll
-      for (int k = 0; k < CPL; ++k) {
-        const float sk = o[k] * nscale;
-        acc = fmaf(sk, sk, acc);
-      }
-      P = C;
-      C = N;
+      ir_row<CPL>(R0, R1, R2, pend, bnext, y, r32, u, b, L, x0, lane, nscale, acc);
+      R0 = R1;
+      R1 = R2;
     }
   }
   const double s = block_sum((double)acc);
@@ -521,9 +575,10 @@ cudaError_t launch_ir_strip(float* r32, const double* u, const double* b, const 
     k_ir_strip3<<<blocks, kIrThreads, 0, stream>>>(r32, u, b, L, nsp, partials, zseg);
     return cudaGetLastError();
   }
-  // segments: about four blocks of eight warps per SM, 16..256 rows each (two halo rows per segment)
+  // segments: one wave (kIrMinBlocks2D blocks of eight warps per SM, one segment per warp), 16..256
+  // rows each (two halo rows per segment)
   const int nstrips2 = L.nx / (32 * kIrCpl2D);
-  const int64_t target = (int64_t)sm_count * 4 * kIrWarps;
+  const int64_t target = (int64_t)sm_count * kIrMinBlocks2D * kIrWarps;
   const int64_t per_strip = std::max<int64_t>(1, target / nstrips2);
   const int seg = (int)std::min<int64_t>(256, std::max<int64_t>(16, (L.ny + per_strip - 1) / per_strip));
   const int64_t ntasks = (int64_t)nstrips2 * ((L.ny + seg - 1) / seg);

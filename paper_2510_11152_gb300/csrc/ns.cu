@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -522,6 +523,14 @@ fas_status ns_projection_step(ns_ctx* c, double* const fields[8], const double* 
   for (int a = 0; a < dim; ++a)
     if (!cnew[a] || !cold[a]) return ns_fail(FAS_EINVAL, "ns_projection_step: missing velocity field");
   if (!Pn || !Po) return ns_fail(FAS_EINVAL, "ns_projection_step: missing pressure field");
+  // every field moves through the solver's 16-byte vector accesses
+  for (int k = 0; k < 8; ++k)
+    if ((dim == 3 || (k != 4 && k != 5)) && (reinterpret_cast<uintptr_t>(fields[k]) & 15u))
+      return ns_fail(FAS_EINVAL, "ns_projection_step: field not 16-byte aligned");
+  if (force)
+    for (int a = 0; a < dim; ++a)
+      if (reinterpret_cast<uintptr_t>(force[a]) & 15u)
+        return ns_fail(FAS_EINVAL, "ns_projection_step: force field not 16-byte aligned");
   if (info) std::memset(info, 0, 4 * sizeof(fas_info));
   const NsGrid& G = c->G;
   const size_t bytes = (size_t)G.cells * sizeof(double);

@@ -28,6 +28,7 @@
 
 #include "bits64.cuh"
 #include "common.cuh"
+#include "cp_async.cuh"
 #include "stream2d.h"
 
 namespace fasmg {
@@ -185,18 +186,6 @@ struct Ring<true> {  // the post-smoothing kernel that also updates a float64 fi
   float4 f[kPF][32];
   double2 w[kPF][2][32];  // float64 solution row, two halves of the lane's 4 cells
 };
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  const int bytes = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Issue the copies of row y (u only when load_u) into ring slot `slot`, then commit the group.
 template <bool FAST, bool UPD>

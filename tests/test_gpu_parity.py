@@ -171,6 +171,7 @@ def test_singular_poisson_coarse_exact(cuda_lib):
 
 
 def test_error_statuses(cuda_lib):
+    import torch
     fas = cuda_lib
     p = fas.make_params((48, 64), 1.0 / 64)
     with pytest.raises(fas.FasError) as e:
@@ -193,3 +194,11 @@ def test_error_statuses(cuda_lib):
     with pytest.raises(fas.FasError) as e:
         fas.fas_solve(ctx2, _t(np.zeros((64, 64))), _t(bad))
     assert e.value.status in (fas.FAS_ENONFINITE, fas.FAS_ENOTCONV)
+    # fields are moved in 16-byte vectors: a view starting at an odd element is rejected, not run
+    big = _t(np.zeros(64 * 64 + 1))
+    with pytest.raises(fas.FasError) as e:
+        fas.fas_solve(ctx2, big[1:], f)
+    assert e.value.status == fas.FAS_EINVAL and "aligned" in str(e.value)
+    with pytest.raises(fas.FasError) as e:
+        fas.fas_residual_ir(ctx2, ug, big[1:], torch.empty(64 * 64, dtype=torch.float32, device="cuda"))
+    assert e.value.status == fas.FAS_EINVAL

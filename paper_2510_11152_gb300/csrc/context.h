@@ -74,6 +74,7 @@ struct fas_ctx {
   double* partials = nullptr;  // per-block partial sums
   int max_blocks = 0;
   double* d_scalar = nullptr;  // small device scalars
+  unsigned* ir_ticket = nullptr;  // work counter and finished-block count of the refinement residual
   double* h_scalar = nullptr;  // pinned host mirror
   double* b = nullptr;         // heat-step right-hand side (fine, float64)
   double* fproj = nullptr;     // mean-free copy of f for singular problems

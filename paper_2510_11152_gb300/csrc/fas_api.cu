@@ -629,7 +629,7 @@ int launch_ir_residual(fas_ctx* c, float* r32, const double* u, const double* b,
   int g = grid_for(c, n);
   Prof pr(c, FAS_K_IR, 0, (double)n);
   if (ir_strip_supported(L))
-    launch_ir_strip(r32, u, b, L, nsp, c->partials, c->sm_count, c->max_blocks, &g, c->stream);
+    launch_ir_strip(r32, u, b, L, nsp, c->partials, c->ir_ticket, c->sm_count, c->max_blocks, &g, c->stream);
   else if (c->p.dim == 2)
     k_ir_residual<2><<<g, kBlock, 0, c->stream>>>(r32, u, b, L, nsp, c->partials);
   else
@@ -1222,6 +1222,9 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
   };
   if (cudaMalloc(&c->partials, c->max_blocks * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "partials"));
   if (cudaMalloc(&c->d_scalar, 8 * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "scalars"));
+  if (cudaMalloc(&c->ir_ticket, 2 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(c->ir_ticket, 0, 2 * sizeof(unsigned)) != cudaSuccess)
+    return bail(fail(FAS_ENOMEM, "work counter"));
   if (cudaMallocHost(&c->h_scalar, 8 * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "pinned"));
   if (cudaMalloc(&c->S, sizeof(SolveState)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "solve state"));
   if (cudaMallocHost(&c->Sh, sizeof(SolveState)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "pinned state"));
@@ -1256,6 +1259,7 @@ fas_status fas_destroy(fas_ctx* c) {
   free_hier(c->h32);
   if (c->partials) cudaFree(c->partials);
   if (c->d_scalar) cudaFree(c->d_scalar);
+  if (c->ir_ticket) cudaFree(c->ir_ticket);
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
   if (c->b) cudaFree(c->b);
   if (c->fproj) cudaFree(c->fproj);

@@ -29,6 +29,7 @@ constexpr int kIrThreads = 32 * kIrWarps;
 constexpr int kIrCols = 128;  // columns per strip of the 3D kernel (4 per lane); 2D strips are 32 CPL wide
 constexpr int kIrCpl2D = 4;   // cells per lane of the 2D kernel
 constexpr int kIrMinBlocks2D = 2;
+constexpr int kIrTasksPerWarp = 6;  // 2D work items per warp, taken dynamically
 constexpr unsigned kAll = 0xffffffffu;
 constexpr int kExpNone = 1 << 20;  // neutral bounds of an absent row; -kExpNone marks a bad value
 
@@ -302,11 +303,14 @@ __device__ __forceinline__ void ir_row(const IrRowM<CPL>& P, const IrRowM<CPL>& 
   }
 }
 
-// 2D: one warp per strip of 32 CPL columns, walking a segment of rows.
+// 2D: a warp takes tasks (a strip of 32 CPL columns and a segment of rows) from ticket[0] until none
+// is left; the last block to finish sets both counters back to zero for the next launch. Segments near
+// a sign change of u cost more (their rows take the float64 path), so tasks are handed out as warps
+// become free instead of in a fixed share.
 template <int CPL, int MINB>
 __global__ void __launch_bounds__(kIrThreads, MINB)
     k_ir_strip(float* __restrict__ r32, const double* __restrict__ u, const double* __restrict__ b, LevelDesc<double> L,
-               const float* nsp, double* partials, int seg) {
+               const float* nsp, double* partials, unsigned* ticket, int seg) {
   constexpr int COLS = 32 * CPL;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -316,7 +320,12 @@ __global__ void __launch_bounds__(kIrThreads, MINB)
   const int ntasks = nstrips * nseg;
   const float nscale = nsp ? *nsp : 1.f;
   float acc = 0.f;
-  for (int task = blockIdx.x * kIrWarps + warp; task < ntasks; task += gridDim.x * kIrWarps) {
+  (void)warp;
+  for (;;) {
+    unsigned tk = 0;
+    if (lane == 0) tk = atomicAdd(ticket, 1u);
+    const int task = (int)__shfl_sync(kAll, tk, 0);
+    if (task >= ntasks) break;
     const int sx = task % nstrips, sy = task / nstrips;
     const int x0 = sx * COLS + CPL * lane;
     const int y0 = sy * seg, y1 = min(ny, y0 + seg);
@@ -337,8 +346,15 @@ __global__ void __launch_bounds__(kIrThreads, MINB)
       R1 = R2;
     }
   }
-  const double s = block_sum((double)acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  const double s = block_sum((double)acc);  // every warp of the block has left the task loop
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = s;
+    __threadfence();
+    if (atomicAdd(ticket + 1, 1u) == gridDim.x - 1) {  // the last block: no warp takes tasks any more
+      ticket[0] = 0u;
+      ticket[1] = 0u;
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -561,8 +577,8 @@ bool ir_strip_supported(const LevelDesc<double>& L) {
 }
 
 cudaError_t launch_ir_strip(float* r32, const double* u, const double* b, const LevelDesc<double>& L,
-                            const float* nsp, double* partials, int sm_count, int max_blocks, int* nblocks,
-                            cudaStream_t stream) {
+                            const float* nsp, double* partials, unsigned* ticket, int sm_count, int max_blocks,
+                            int* nblocks, cudaStream_t stream) {
   const int nstrips = L.nx / kIrCols;
   if (L.nz > 1) {
     // blocks of eight rows y; z segments sized for about four blocks per SM, 8..128 planes each
@@ -575,16 +591,18 @@ cudaError_t launch_ir_strip(float* r32, const double* u, const double* b, const 
     k_ir_strip3<<<blocks, kIrThreads, 0, stream>>>(r32, u, b, L, nsp, partials, zseg);
     return cudaGetLastError();
   }
-  // segments: one wave (kIrMinBlocks2D blocks of eight warps per SM, one segment per warp), 16..256
-  // rows each (two halo rows per segment)
+  // one wave of kIrMinBlocks2D blocks of eight warps per SM; segments of 16..256 rows (two halo rows
+  // each) sized for about kIrTasksPerWarp tasks per warp
   const int nstrips2 = L.nx / (32 * kIrCpl2D);
-  const int64_t target = (int64_t)sm_count * kIrMinBlocks2D * kIrWarps;
-  const int64_t per_strip = std::max<int64_t>(1, target / nstrips2);
+  const int64_t warps = (int64_t)sm_count * kIrMinBlocks2D * kIrWarps;
+  const int64_t per_strip = std::max<int64_t>(1, warps * kIrTasksPerWarp / nstrips2);
   const int seg = (int)std::min<int64_t>(256, std::max<int64_t>(16, (L.ny + per_strip - 1) / per_strip));
   const int64_t ntasks = (int64_t)nstrips2 * ((L.ny + seg - 1) / seg);
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(max_blocks, (ntasks + kIrWarps - 1) / kIrWarps));
+  const int64_t want = (ntasks + kIrWarps - 1) / kIrWarps;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(max_blocks, want),
+                                                                   (int64_t)sm_count * kIrMinBlocks2D));
   *nblocks = blocks;
-  k_ir_strip<kIrCpl2D, kIrMinBlocks2D><<<blocks, kIrThreads, 0, stream>>>(r32, u, b, L, nsp, partials, seg);
+  k_ir_strip<kIrCpl2D, kIrMinBlocks2D><<<blocks, kIrThreads, 0, stream>>>(r32, u, b, L, nsp, partials, ticket, seg);
   return cudaGetLastError();
 }
 

@@ -12,9 +12,10 @@ namespace fasmg {
 bool ir_strip_supported(const LevelDesc<double>& L);
 
 // r32 = (float)(b - A u) and per-block partials of sum (s r32)^2 (s = *nsp, or 1) into
-// partials[0 .. *nblocks). At most max_blocks blocks are launched.
+// partials[0 .. *nblocks). At most max_blocks blocks are launched. ticket: two zeroed counters the 2D
+// kernel hands out its work with (it leaves them zero again); launches sharing them must not overlap.
 cudaError_t launch_ir_strip(float* r32, const double* u, const double* b, const LevelDesc<double>& L,
-                            const float* nsp, double* partials, int sm_count, int max_blocks, int* nblocks,
-                            cudaStream_t stream);
+                            const float* nsp, double* partials, unsigned* ticket, int sm_count, int max_blocks,
+                            int* nblocks, cudaStream_t stream);
 
 }  // namespace fasmg

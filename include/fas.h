@@ -190,7 +190,10 @@ fas_status fas_residual(fas_ctx* ctx, int level, const double* u, const double* 
  * S = sum_nb u_nb - M u (M the diagonal's neighbour count plus boundary multiplicities) is summed
  * exactly in integer arithmetic on the significands and rounded once; cells whose stencil holds a
  * zero, a subnormal or non-finite value, or values more than 2^5 apart in exponent, use the float64
- * expression of fas_residual. u, f DEVICE float64, r32 DEVICE float32, nx*ny(*nz) each. */
+ * expression of fas_residual (2D levels with nx a multiple of 128 decide per row of 128 cells, and
+ * also take that expression for rows holding values of both signs). r32 is reproducible bit for bit;
+ * norm2 sums float32 partials whose grouping depends on how the GPU scheduled the work, so its last
+ * bits may vary between calls. u, f DEVICE float64, r32 DEVICE float32, nx*ny(*nz) each. */
 fas_status fas_residual_ir(fas_ctx* ctx, const double* u, const double* f, float* r32, double* norm2);
 
 /* `sweeps` X-MCGS sweeps in place on u of level `level` (Sec. 2.3 / Appendix B). */

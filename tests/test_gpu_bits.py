@@ -153,3 +153,25 @@ def test_refinement_residual_exact(cuda_lib, shape, kind, bc, alpha, beta, fax, 
         scale = abs(float(f[nidx])) + (abs(alpha) + 12 * c) * abs(float(u[nidx])) + 1e-300
         assert abs(float(got[nidx]) - ref) <= 2.0 ** -23 * abs(ref) + 1e-13 * scale, idx
     assert n_exact >= cover * n_cells, (n_exact, n_cells)
+
+
+def test_refinement_residual_is_reproducible(cuda_lib):
+    """The 2D strip kernel hands its segments to whichever warp is free: r32 must not depend on that
+    assignment (bit for bit); the norm sums per-block partials whose float32 accumulation order
+    does, so only its last bits may vary."""
+    import torch
+    fas = cuda_lib
+    shape = (1024, 1024)
+    u = noisy_cos_mode(shape, 611)  # crosses zero: some segments take the float64 path
+    f = u + 1e-3 * random_field(shape, 612, -1, 1)
+    ctx = fas.fas_create(fas.make_params(shape, 1.0 / 1024, alpha=1.0, beta=1e-4, precision=fas.FAS_MIXED))
+    ut, ft = _t(u), _t(f)
+    r32 = torch.empty(u.size, dtype=torch.float32, device="cuda")
+    first = fas.fas_residual_ir(ctx, ut, ft, r32)
+    r_first = r32.clone()
+    ref = float(np.linalg.norm(r_first.cpu().numpy().astype(np.float64)))
+    assert abs(first - ref) <= 1e-6 * ref
+    for _ in range(6):
+        nrm = fas.fas_residual_ir(ctx, ut, ft, r32)
+        assert abs(nrm - first) <= 1e-9 * first
+        assert torch.equal(r32, r_first)

@@ -359,7 +359,9 @@ __global__ void __launch_bounds__(kIrThreads, MINB)
 // walks a segment of planes z with the planes z-1, z, z+1 of its row unpacked in registers; the rows
 // y-1 and y+1 of the current plane are read by the neighbouring warps of the block too (eight
 // consecutive rows per block), so they come from L1. Exact zeros (the wall slots of face grids, a
-// fluid at rest) are exact values here: significand 0, outside the exponent range.
+// fluid at rest) are exact values here: significand 0, outside the exponent range. Each lane decides
+// for its own four cells whether their stencils' values (its window of 22) qualify for the exact
+// sum: a 3D row of 128 cells of a smooth field spans more than 2^5 far more often than that.
 // ------------------------------------------------------------------------------------------------
 constexpr int kIr3Rows = kIrWarps;  // rows y per block
 
@@ -414,8 +416,8 @@ __device__ __forceinline__ void load_row3(IrRow3& R, const double* __restrict__ 
       R.E[k] = 0;
     }
   }
-  R.lo = __reduce_min_sync(kAll, bad ? -kExpNone : lo);
-  R.hi = __reduce_max_sync(kAll, hi);
+  R.lo = bad ? -kExpNone : lo;  // this lane's values only: the exact path is decided per lane
+  R.hi = hi;
 }
 
 __global__ void __launch_bounds__(kIrThreads, 2)
@@ -451,32 +453,51 @@ __global__ void __launch_bounds__(kIrThreads, 2)
       const double2 b23 = reinterpret_cast<const double2*>(b + cb)[1];
       const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
       double r[4];
-      const int Eref = min(min(C.lo, min(P.lo, N.lo)), min(S.lo, T.lo));
-      const int Etop = max(max(C.hi, max(P.hi, N.hi)), max(S.hi, T.hi));
-      // an all-zero stencil window has Eref = kExpNone: any exponent works, use 1
+      // The lane's window: its four cells in the five rows and their two horizontal neighbours (from
+      // the adjacent lanes, or the strip's outer neighbours on lanes 0 and 31), unpacked.
+      long long sw = __shfl_up_sync(kAll, (long long)C.sig[3], 1);
+      int ew = __shfl_up_sync(kAll, C.E[3], 1);
+      long long se = __shfl_down_sync(kAll, (long long)C.sig[0], 1);
+      int ee = __shfl_down_sync(kAll, C.E[0], 1);
+      if (lane == 0 || lane == 31) {
+        int64_t hs = 0;
+        int Eh = 0, l0 = 0, h0 = 0;
+        bool bd = false;
+        unpack_z(C.halo, hs, Eh, l0, h0, bd);  // 0 where the strip has no outer neighbour
+        if (lane == 0) {
+          sw = hs;
+          ew = Eh;
+        } else {
+          se = hs;
+          ee = Eh;
+        }
+      }
+      int Eref = min(min(C.lo, min(P.lo, N.lo)), min(S.lo, T.lo));
+      int Etop = max(max(C.hi, max(P.hi, N.hi)), max(S.hi, T.hi));
+      if (sw != 0) {
+        Eref = bad_exp(ew) ? -kExpNone : min(Eref, ew);
+        Etop = max(Etop, ew);
+      }
+      if (se != 0) {
+        Eref = bad_exp(ee) ? -kExpNone : min(Eref, ee);
+        Etop = max(Etop, ee);
+      }
+      // an all-zero window has Eref = kExpNone: any exponent works, use 1
       const int Eb = Eref == kExpNone ? 1 : Eref;
-      bool exact = Etop - Eref <= kMaxExpSpread || Eref == kExpNone;
-      if (exact) {
+      const bool want = Etop - Eref <= kMaxExpSpread || Eref == kExpNone;
+      bool ok = want;
+      if (want) {  // per lane; nothing below synchronises the warp
         int64_t Xc[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) Xc[k] = align_z(C.sig[k], C.E[k], Eb);
-        long long wl = __shfl_up_sync(kAll, (long long)Xc[3], 1);
-        long long er = __shfl_down_sync(kAll, (long long)Xc[0], 1);
-        if (lane == 0 || lane == 31) {
-          int64_t hs = 0;
-          int Eh = 0, l0 = 0, h0 = 0;
-          bool bd = false;
-          unpack_z(C.halo, hs, Eh, l0, h0, bd);
-          const int64_t hx = align_z(hs, Eh, Eb);
-          if (lane == 0) wl = hx;
-          else er = hx;
-        }
-        const bool inner = y > 0 && y < ny - 1 && z > 0 && z < nz - 1;  // the same on every lane
+        const int64_t wl = align_z(sw, ew, Eb), er = align_z(se, ee, Eb);
+        const bool inner = y > 0 && y < ny - 1 && z > 0 && z < nz - 1;
         int64_t Sx[4];
+        bool small = true;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const int64_t Xw = k ? Xc[k - 1] : (int64_t)wl;
-          const int64_t Xe = k < 3 ? Xc[k + 1] : (int64_t)er;
+          const int64_t Xw = k ? Xc[k - 1] : wl;
+          const int64_t Xe = k < 3 ? Xc[k + 1] : er;
           const int64_t V = (align_z(S.sig[k], S.E[k], Eb) + align_z(T.sig[k], T.E[k], Eb)) +
                             (align_z(P.sig[k], P.E[k], Eb) + align_z(N.sig[k], N.E[k], Eb));
           int M = 6;
@@ -485,49 +506,29 @@ __global__ void __launch_bounds__(kIrThreads, 2)
             M = (int)L.mt[cls];
           }
           Sx[k] = (Xw + Xe) + V - (int64_t)M * Xc[k];
-        }
-        bool small = true;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
           small = small && (uint64_t)(Sx[k] + ((1ll << 53) - 1)) < (1ull << 54) - 1ull;
-        bool ok = true;
-        if (__all_sync(kAll, small)) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            double Sd;
-            ok = fixed_to_f64_small(Sx[k], Eb, &Sd) && ok;
-            r[k] = fma(L.c, Sd, fma(-L.alpha, as_d(repack(C.sig[k], C.E[k])), bv[k]));
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            double Sd;
-            ok = fixed_to_f64(Sx[k], Eb, &Sd) && ok;
-            r[k] = fma(L.c, Sd, fma(-L.alpha, as_d(repack(C.sig[k], C.E[k])), bv[k]));
-          }
         }
-        exact = !__any_sync(kAll, !ok);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          double Sd;
+          ok = (small ? fixed_to_f64_small(Sx[k], Eb, &Sd) : fixed_to_f64(Sx[k], Eb, &Sd)) && ok;
+          r[k] = fma(L.c, Sd, fma(-L.alpha, as_d(repack(C.sig[k], C.E[k])), bv[k]));
+        }
       }
-      if (!exact) {  // the float64 point equation, as in residual_point, from the values in memory
-        const double2* pc = reinterpret_cast<const double2*>(u + cb);
-        const double c4[4] = {pc[0].x, pc[0].y, pc[1].x, pc[1].y};
-        double wv = __shfl_up_sync(kAll, c4[3], 1);
-        double ev = __shfl_down_sync(kAll, c4[0], 1);
-        if (lane == 0 && x0 > 0) wv = u[cb - 1];
-        if (lane == 31 && x0 + 4 < nx) ev = u[cb + 4];
+      if (!ok) {  // the float64 point equation, as in residual_point, from the values in memory
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int x = x0 + k;
           const int64_t q = cb + k;
-          const double w = x > 0 ? (k ? c4[k - 1] : wv) : 0.0;
-          const double e = x < nx - 1 ? (k < 3 ? c4[k + 1] : ev) : 0.0;
+          const double w = x > 0 ? u[q - 1] : 0.0;
+          const double e = x < nx - 1 ? u[q + 1] : 0.0;
           const double sv = y > 0 ? u[q - sy] : 0.0;
           const double nv = y < ny - 1 ? u[q + sy] : 0.0;
           const double bo = z > 0 ? u[q - sz] : 0.0;
           const double to = z < nz - 1 ? u[q + sz] : 0.0;
           const double nb = ((w + e) + (sv + nv)) + (bo + to);
           const int cls = bclass<3>(x, y, z, nx, ny, nz);
-          r[k] = fma(L.c, nb, fma(-L.d[cls], c4[k], bv[k]));
+          r[k] = fma(L.c, nb, fma(-L.d[cls], u[q], bv[k]));
         }
       }
       // frozen wall slots of a face grid: residual 0

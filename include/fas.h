@@ -144,9 +144,11 @@ fas_status fas_heat_adjoint(fas_ctx* ctx, const double* u0, const double* fsrc, 
                             const double* dL_duT, double* uT, double* g_u0, double* g_f, double* g_kappa,
                             int ckpt_every);
 
-/* fas_heat_run with HOST buffers (pinned memory gives the fastest copies): copies u0_host and
- * fsrc_host (may be NULL) to device buffers the context keeps between calls, runs nsteps steps and
- * copies the result to uT_host (may equal u0_host). Returns after the result is on the host. */
+/* fas_heat_run with HOST buffers: copies u0_host and fsrc_host (may be NULL) to device buffers the
+ * context keeps between calls, runs nsteps steps and copies the result to uT_host (may equal
+ * u0_host). Returns after the result is on the host. Page-locked buffers that the GPU can address
+ * (cudaHostAlloc / PyTorch pin_memory under unified addressing, 16-byte aligned) are copied by the
+ * GPU's own loads and stores over the host link; other buffers by cudaMemcpyAsync. */
 fas_status fas_heat_run_host(fas_ctx* ctx, const double* u0_host, double* uT_host,
                              const double* fsrc_host, double dt, int nsteps, fas_info* infos);
 

@@ -202,3 +202,39 @@ def test_error_statuses(cuda_lib):
     with pytest.raises(fas.FasError) as e:
         fas.fas_residual_ir(ctx2, ug, big[1:], torch.empty(64 * 64, dtype=torch.float32, device="cuda"))
     assert e.value.status == fas.FAS_EINVAL
+
+
+@pytest.mark.parametrize("pinned,with_src,alias", [(True, True, False), (False, True, False), (True, False, True),
+                                                   (False, False, True)])
+def test_heat_run_host_matches_device_run(cuda_lib, pinned, with_src, alias):
+    """fas_heat_run_host (host buffers in and out; page-locked buffers are copied by the GPU's own
+    loads and stores, pageable ones by cudaMemcpyAsync) equals fas_heat_run on device buffers bit for
+    bit, including uT_host aliasing u0_host."""
+    import torch
+    fas = cuda_lib
+    shape = (256, 256)
+    dt = 1e-3
+    u0 = noisy_cos_mode(shape, 261)
+    src = random_field(shape, 262, -1, 1) if with_src else None
+    params = dict(alpha=1.0, beta=dt, precision=fas.FAS_MIXED)
+    ref_ctx = fas.fas_create(fas.make_params(shape, 1.0 / 256, **params))
+    ud = _t(u0)
+    fas.fas_heat_run(ref_ctx, ud, None if src is None else _t(src), dt, 3)
+    ctx = fas.fas_create(fas.make_params(shape, 1.0 / 256, **params))
+
+    keep = []  # the host tensors behind the numpy views stay alive for the whole test
+
+    def host(a):
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        t = t.pin_memory() if pinned else t.clone()
+        keep.append(t)
+        return t.numpy()
+
+    u0h = host(u0)
+    outh = u0h if alias else host(np.zeros(shape))
+    fh = None if src is None else host(src)
+    for _ in range(2):  # the second call reuses the context's device buffers
+        if alias:
+            u0h[...] = u0
+        fas.fas_heat_run_host(ctx, u0h, outh, fh, dt, 3)
+        assert np.array_equal(outh, ud.cpu().numpy())

@@ -87,7 +87,15 @@ typedef struct {
   int seg_rows;          /* rows per warp segment in the fused 2D kernels (0: default 128)      */
   int location;          /* fas_location (default FAS_CELL). Face grids need kappa == NULL and
                           * coarse_exact 0; they run the per-operation kernels                  */
+  int ordering;          /* fas_ordering of the X-MCGS sweeps (default FAS_ORDER_FORWARD)       */
 } fas_params;
+
+/* X-MCGS sweep orderings (Sec. 2.3, the smoother comparison). FORWARD ("1234-1234"): every sweep
+ * updates the parity sets in the paper's order, sets 1-2 (2D; 1-4 in 3D: odd index sum) then the
+ * rest. SYMMETRIC ("1234-4321"): the sweeps of each smoothing step alternate forward and backward
+ * (sets in reverse order), the symmetric Gauss-Seidel analogue; cell-centred unknowns only, and it
+ * runs the per-operation kernels. */
+typedef enum { FAS_ORDER_FORWARD = 0, FAS_ORDER_SYMMETRIC = 1 } fas_ordering;
 
 /* Per-solve report. res0/res are ||f - A u||_2 before the first and after the last cycle
  * (the paper's h-weighted value when tol_relative == 0); rel = res / ||f||_2; rho is the mean

@@ -8,7 +8,9 @@ Follows the paper section by section:
   * FAS two-grid solver ............. Algorithm 1 (TMGSolver), with the recursion of the remark that
                                       follows it (coarse steps replaced by a recursive call)
   * X-MCGS smoother ................. Sec. 2.3, Eqs. FCGS-1..FCGS-4 (2D, four parity sets in order
-                                      1,2,3,4); Appendix B (3D, eight parity sets in order 1..8)
+                                      1,2,3,4); Appendix B (3D, eight parity sets in order 1..8);
+                                      the symmetric "1234-4321" ordering of the smoother comparison
+                                      in Sec. 2.3 (forward and backward sweeps alternating)
   * restriction / prolongation ...... Appendix C (four-point average, piecewise-constant injection;
                                       3D analogues with eight children)
   * heat stepping ................... Sec. 1 (backward Euler, new step overwrites the old)
@@ -89,6 +91,7 @@ class Params:
     tol_mode: str = "relative"  # or "absolute" (paper's h-weighted norm, Eq. residual)
     coarsest: int = 4  # cells along the shortest axis of the coarsest level
     coarse_exact: bool = False
+    ordering: str = "1234-1234"  # or "1234-4321": each smoothing step alternates forward/backward sweeps
 
     def sweeps_coarse(self):
         return self.nu1 if self.nu_coarse is None else self.nu_coarse
@@ -264,12 +267,18 @@ def xmcgs_sweep(op: Operator, u: np.ndarray, f: np.ndarray,
 
 
 def smooth(op: Operator, u: np.ndarray, f: np.ndarray, sweeps: int,
-           coef: SmootherCoefficients | None = None) -> None:
-    """S applied `sweeps` times (the inner loops m = 1..s of Algorithm 1)."""
+           coef: SmootherCoefficients | None = None, ordering: str = "1234-1234") -> None:
+    """S applied `sweeps` times (the inner loops m = 1..s of Algorithm 1). ordering "1234-1234":
+    every sweep visits the sets in the paper's order; "1234-4321" (Sec. 2.3, the symmetric variant
+    compared with it): the second, fourth, ... sweep visits them in reverse order."""
+    if ordering not in ("1234-1234", "1234-4321"):
+        raise ValueError("ordering must be '1234-1234' or '1234-4321'")
     if coef is None:
         coef = smoother_coefficients(op)
-    for _ in range(sweeps):
-        xmcgs_sweep(op, u, f, coef)
+    forward = SETS_2D if op.dim == 2 else SETS_3D
+    for m in range(sweeps):
+        backward = ordering == "1234-4321" and m % 2 == 1
+        xmcgs_sweep(op, u, f, coef, sets=forward[::-1] if backward else forward)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -330,7 +339,7 @@ def coarsest_solve(op: Operator, u: np.ndarray, f: np.ndarray, params: Params) -
     """Coarsest level (reading G6): s X-MCGS sweeps (the paper's remark replacing the direct
     solve), or an exact dense solve (least-squares / minimum norm when singular, reading G7)."""
     if not params.coarse_exact:
-        smooth(op, u, f, params.sweeps_coarse())
+        smooth(op, u, f, params.sweeps_coarse(), ordering=params.ordering)
         return
     M = dense_matrix(op)
     rhs = np.asarray(f, dtype=np.float64).ravel()
@@ -349,7 +358,7 @@ def vcycle(levels: list, u: np.ndarray, f: np.ndarray, params: Params, level: in
         coarsest_solve(op, u, f, params)
         return
     coef = smoother_coefficients(op)
-    smooth(op, u, f, params.nu1, coef)  # fine-grid pre-smoothing
+    smooth(op, u, f, params.nu1, coef, params.ordering)  # fine-grid pre-smoothing
     r1 = residual(op, u, f)  # fine-grid point-wise residual
     u0 = restrict(u)  # coarse-grid approximation p0 = R(p1)
     r0 = restrict(r1)  # r0 = R(r1)
@@ -358,7 +367,7 @@ def vcycle(levels: list, u: np.ndarray, f: np.ndarray, params: Params, level: in
     vcycle(levels, u0, f0, params, level + 1)  # coarse problem, recursively
     c0 = u0 - u0_start  # coarse-grid correction
     u += prolong(c0)  # fine-grid correction
-    smooth(op, u, f, params.nu2, coef)  # fine-grid post-smoothing
+    smooth(op, u, f, params.nu2, coef, params.ordering)  # fine-grid post-smoothing
 
 
 @dataclass

@@ -31,6 +31,7 @@ STATUS_NAMES = ["FAS_OK", "FAS_EINVAL", "FAS_ENOMEM", "FAS_ENOTCONV", "FAS_ENONF
                 "FAS_ECUDA", "FAS_EUNSUPPORTED"]
 FAS_BC_NEUMANN, FAS_BC_DIRICHLET = 0, 1
 FAS_FP64, FAS_MIXED = 0, 1
+FAS_ORDER_FORWARD, FAS_ORDER_SYMMETRIC = 0, 1  # X-MCGS 1234-1234 / 1234-4321 (Sec. 2.3)
 FAS_CELL, FAS_FACE_X, FAS_FACE_Y, FAS_FACE_Z = 0, 1, 2, 3
 
 
@@ -43,7 +44,7 @@ class fas_params(ctypes.Structure):
         ("coarsest", ctypes.c_int), ("coarse_exact", ctypes.c_int), ("tol", ctypes.c_double),
         ("tol_relative", ctypes.c_int), ("precision", ctypes.c_int), ("inner_cycles", ctypes.c_int),
         ("use_graph", ctypes.c_int), ("path", ctypes.c_int), ("seg_rows", ctypes.c_int),
-        ("location", ctypes.c_int),
+        ("location", ctypes.c_int), ("ordering", ctypes.c_int),
     ]
 
 

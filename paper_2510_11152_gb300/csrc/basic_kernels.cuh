@@ -574,14 +574,20 @@ struct CoarseArgs {
   T* const* u0;
   const T* cinv;  // dense inverse of the coarsest operator, or null
   int l0, nlev, nu1, nu2, nuc;
+  int ordering;  // fas_ordering
 };
 
+// Colour updated first by sweep s of a smoothing step: the odd index sums (sets 1-2 in 2D, 1-4 in
+// 3D) for a forward sweep; a symmetric ordering runs every second sweep backward.
+__host__ __device__ __forceinline__ int first_colour(int ordering, int s) { return (ordering == 1 && (s & 1)) ? 0 : 1; }
+
 template <typename T, int DIM>
-__device__ void coarse_smooth(T* u, const T* f, const LevelDesc<T>& L, int sweeps) {
+__device__ void coarse_smooth(T* u, const T* f, const LevelDesc<T>& L, int sweeps, int ordering) {
   for (int s = 0; s < sweeps; ++s) {
-    smooth_colour_range<T, DIM>(u, f, L, 1, threadIdx.x, blockDim.x);
+    const int c0 = first_colour(ordering, s);
+    smooth_colour_range<T, DIM>(u, f, L, c0, threadIdx.x, blockDim.x);
     __syncthreads();
-    smooth_colour_range<T, DIM>(u, f, L, 0, threadIdx.x, blockDim.x);
+    smooth_colour_range<T, DIM>(u, f, L, 1 - c0, threadIdx.x, blockDim.x);
     __syncthreads();
   }
 }
@@ -697,7 +703,7 @@ __global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayou
     const LevelDesc<T>& L = sdesc[l];
     T* u = sm + S.off_u[l];
     const T* f = sm + S.off_f[l];
-    coarse_smooth<T, DIM>(u, f, L, A.nu1);
+    coarse_smooth<T, DIM>(u, f, L, A.nu1, A.ordering);
     if constexpr (FAX < 0)
       restrict_resid_range<T, DIM>(sm + S.off_u[l + 1], sm + S.off_u0[l + 1], sm + S.off_f[l + 1], u, f, L,
                                    threadIdx.x, blockDim.x);
@@ -722,7 +728,7 @@ __global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayou
       }
       __syncthreads();
     } else {
-      coarse_smooth<T, DIM>(u, f, L, A.nuc);
+      coarse_smooth<T, DIM>(u, f, L, A.nuc, A.ordering);
     }
   }
   for (int l = last - 1; l >= A.l0; --l) {
@@ -735,7 +741,7 @@ __global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayou
       prolong_face_range<T, DIM, FAX>(u, sm + S.off_u[l + 1], sm + S.off_u0[l + 1], L.nx, L.ny, L.nz, threadIdx.x,
                                       blockDim.x);
     __syncthreads();
-    coarse_smooth<T, DIM>(u, f, L, A.nu2);
+    coarse_smooth<T, DIM>(u, f, L, A.nu2, A.ordering);
   }
   {
     const LevelDesc<T>& L = sdesc[A.l0];

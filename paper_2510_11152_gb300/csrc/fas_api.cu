@@ -360,8 +360,8 @@ fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers)
     // sweep-fused 2D path (float32 only): consecutive levels from the finest that the fused kernels
     // handle and that are larger than the single-CTA switch level
     H.nfast = 0;
-    if (sizeof(T) == 4 && p.dim == 2 && p.path == 0 && !p.kappa && p.location == FAS_CELL && p.nu1 >= 1 &&
-        p.nu2 >= 1) {
+    if (sizeof(T) == 4 && p.dim == 2 && p.path == 0 && !p.kappa && p.location == FAS_CELL &&
+        p.ordering == FAS_ORDER_FORWARD && p.nu1 >= 1 && p.nu2 >= 1) {
       while (H.nfast < H.switch_level &&
              stream2d_supported(c->shape[H.nfast].nx, c->shape[H.nfast].ny, std::max(p.nu1, p.nu2)))
         H.nfast++;
@@ -437,29 +437,16 @@ void launch_prolong(fas_ctx* c, int64_t n, T* u, const T* uc, const T* uc0, int 
 template <typename T, int DIM>
 void launch_smooth(fas_ctx* c, const LevelDesc<T>& L, int level, T* u, const T* f, int sweeps) {
   const int64_t half = (int64_t)(L.nx / 2) * L.ny * L.nz;
-  if (!L.varkappa && L.nx % 4 == 0) {  // 16-byte groups of 4 cells
-    const int g4 = grid_for(c, half / 2);
-    for (int s = 0; s < sweeps; ++s) {
-      {
-        Prof pr(c, FAS_K_SMOOTH, level, (double)half);
-        k_smooth_colour4<T, DIM><<<g4, kBlock, 0, c->stream>>>(u, f, L, 1);
-      }
-      {
-        Prof pr(c, FAS_K_SMOOTH, level, (double)half);
-        k_smooth_colour4<T, DIM><<<g4, kBlock, 0, c->stream>>>(u, f, L, 0);
-      }
-    }
-    return;
-  }
-  const int g = grid_for(c, half);
+  const bool g4ok = !L.varkappa && L.nx % 4 == 0;  // 16-byte groups of 4 cells
+  const int g = grid_for(c, g4ok ? half / 2 : half);
   for (int s = 0; s < sweeps; ++s) {
-    {
+    const int c0 = first_colour(c->p.ordering, s);
+    for (const int colour : {c0, 1 - c0}) {
       Prof pr(c, FAS_K_SMOOTH, level, (double)half);
-      k_smooth_colour<T, DIM><<<g, kBlock, 0, c->stream>>>(u, f, L, 1);
-    }
-    {
-      Prof pr(c, FAS_K_SMOOTH, level, (double)half);
-      k_smooth_colour<T, DIM><<<g, kBlock, 0, c->stream>>>(u, f, L, 0);
+      if (g4ok)
+        k_smooth_colour4<T, DIM><<<g, kBlock, 0, c->stream>>>(u, f, L, colour);
+      else
+        k_smooth_colour<T, DIM><<<g, kBlock, 0, c->stream>>>(u, f, L, colour);
     }
   }
 }
@@ -493,6 +480,7 @@ fas_status launch_coarse(fas_ctx* c, Hier<T>& H, int l0, T* utop, const T* ftop)
   A.nu1 = p.nu1;
   A.nu2 = p.nu2;
   A.nuc = p.nu_coarse > 0 ? p.nu_coarse : p.nu1;
+  A.ordering = p.ordering;
   Prof pr(c, FAS_K_COARSE, l0, (double)c->shape[l0].cells());
   with_fax(c, [&](auto tag) {
     k_coarse_smem<T, DIM, decltype(tag)::value><<<1, kCoarseThreads, H.smem_bytes, c->stream>>>(A, H.smem, utop, ftop);
@@ -1202,6 +1190,7 @@ void fas_default_params(fas_params* p) {
   p->path = 0;
   p->seg_rows = 0;
   p->location = FAS_CELL;
+  p->ordering = FAS_ORDER_FORWARD;
 }
 
 fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
@@ -1220,6 +1209,9 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
   if (!p.kappa && !(p.kappa_const > 0.0)) return fail(FAS_EINVAL, "kappa_const must be positive");
   STATUS_TRY(check_field(p.kappa, false, "fas_create (kappa)"));
   if (p.precision != FAS_FP64 && p.precision != FAS_MIXED) return fail(FAS_EINVAL, "unknown precision");
+  if (p.ordering != FAS_ORDER_FORWARD && p.ordering != FAS_ORDER_SYMMETRIC) return fail(FAS_EINVAL, "unknown ordering");
+  if (p.ordering != FAS_ORDER_FORWARD && p.location != FAS_CELL)
+    return fail(FAS_EUNSUPPORTED, "the symmetric ordering is for cell-centred unknowns");
   for (int k = 0; k < 2 * p.dim; ++k)
     if (p.bc[k] != FAS_BC_NEUMANN && p.bc[k] != FAS_BC_DIRICHLET) return fail(FAS_EINVAL, "unknown bc kind");
   if (p.location < FAS_CELL || p.location > p.dim) return fail(FAS_EINVAL, "location must be a cell or a face axis");

@@ -101,6 +101,8 @@ extern "C" fas_status fas_vcycle_small_static(const fas_params* p, double* u, co
   if (!p || !u || !f) return fail_static(FAS_EINVAL, "fas_vcycle_small_static: null argument");
   if (p->dim != 2 && p->dim != 3) return fail_static(FAS_EINVAL, "fas_vcycle_small_static: dim must be 2 or 3");
   if (ncycles < 1) return fail_static(FAS_EINVAL, "fas_vcycle_small_static: ncycles must be >= 1");
+  if (p->ordering != FAS_ORDER_FORWARD && p->ordering != FAS_ORDER_SYMMETRIC)
+    return fail_static(FAS_EINVAL, "fas_vcycle_small_static: unknown ordering");
   if (p->kappa || p->coarse_exact || p->precision != FAS_FP64 || p->location != FAS_CELL)
     return fail_static(FAS_EUNSUPPORTED,
                        "fas_vcycle_small_static: cell-centred unknowns, constant kappa, smoothed coarsest level "
@@ -194,6 +196,7 @@ extern "C" fas_status fas_vcycle_small_static(const fas_params* p, double* u, co
   A.nu1 = p->nu1;
   A.nu2 = p->nu2;
   A.nuc = p->nu_coarse > 0 ? p->nu_coarse : p->nu1;
+  A.ordering = p->ordering;
   for (int k = 0; k < ncycles; ++k) {
     if (dim == 2) {
       cudaFuncSetAttribute(k_coarse_smem<double, 2, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStaticSmem);

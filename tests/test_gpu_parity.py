@@ -107,6 +107,54 @@ def test_vcycle_iterates(cuda_lib, shape, coarsest, exact, bc_kind):
         assert _rel(_n(ug), u) < 1e-12, "cycle %d" % (k + 1)
 
 
+@pytest.mark.parametrize("shape,coarsest", [((256, 256), 4), ((64, 128), 2), ((32, 32, 32), 2)])
+def test_symmetric_ordering_iterates(cuda_lib, shape, coarsest):
+    """The "1234-4321" X-MCGS ordering (Sec. 2.3): float64 V-cycles against the oracle's, and the
+    mixed-precision solve to the same converged solution; the sweeps alternate direction on every
+    level, the single-CTA levels included."""
+    fas = cuda_lib
+    dim = len(shape)
+    h = 1.0 / shape[-1]
+    op, ctx = _pair(fas, shape, h, 1.0, 2e-3, 1.0, _bc("mixed", dim), coarsest=coarsest,
+                    ordering=fas.FAS_ORDER_SYMMETRIC)
+    prm = cc.Params(coarsest=coarsest, ordering="1234-4321")
+    levels = cc.build_levels(op, coarsest)
+    u = random_field(shape, 221)
+    f = random_field(shape, 222, -1, 1)
+    ug, fg = _t(u), _t(f)
+    for k in range(6):
+        fas.fas_vcycle(ctx, ug, fg)
+        cc.vcycle(levels, u, f, prm)
+        assert _rel(_n(ug), u) < 1e-12, "cycle %d" % (k + 1)
+    # a forward-ordering context gives different iterates
+    _, ctx_fwd = _pair(fas, shape, h, 1.0, 2e-3, 1.0, _bc("mixed", dim), coarsest=coarsest)
+    uf = _t(random_field(shape, 221))
+    fas.fas_vcycle(ctx_fwd, uf, fg)
+    um = _t(random_field(shape, 221))
+    fas.fas_vcycle(ctx, um, fg)
+    assert _rel(_n(um), _n(uf)) > 1e-8
+    # mixed precision reaches the oracle's converged solution
+    _, ctx_m = _pair(fas, shape, h, 1.0, 2e-3, 1.0, _bc("mixed", dim), coarsest=coarsest,
+                     ordering=fas.FAS_ORDER_SYMMETRIC, precision=fas.FAS_MIXED)
+    u_ref = np.zeros(shape)
+    assert cc.solve(levels, u_ref, f, cc.Params(coarsest=coarsest, ordering="1234-4321", tol=1e-13,
+                                                kmax=60)).converged
+    um = _t(np.zeros(shape))
+    assert fas.fas_solve(ctx_m, um, fg).converged
+    assert _rel(_n(um), u_ref) < 1e-9
+
+
+def test_symmetric_ordering_argument_checks(cuda_lib):
+    fas = cuda_lib
+    with pytest.raises(fas.FasError) as e:
+        fas.fas_create(fas.make_params((64, 64), 1.0 / 64, ordering=2))
+    assert e.value.status == fas.FAS_EINVAL
+    with pytest.raises(fas.FasError) as e:
+        fas.fas_create(fas.make_params((64, 64), 1.0 / 64, ordering=fas.FAS_ORDER_SYMMETRIC,
+                                       location=fas.FAS_FACE_X))
+    assert e.value.status == fas.FAS_EUNSUPPORTED
+
+
 def test_vcycle_iterates_variable_kappa(cuda_lib):
     fas = cuda_lib
     shape = (128, 128)

@@ -150,15 +150,16 @@ def test_each_set_update_zeroes_its_residual(dim, bc_kind, var_kappa):
         assert np.max(np.abs(r[cell])) < 1e-13 * scale
 
 
-def _rbgs_literal(op, u, f):
+def _rbgs_literal(op, u, f, colours=(1, 0)):
     """Point-by-point red-black Gauss-Seidel (Appendix A): all points with i+j(+l) odd, then all
-    with i+j(+l) even, each solved exactly for its own value with its neighbours' current values.
-    Written independently of the oracle: scalar loops, ghost relation solved per point."""
+    with i+j(+l) even (or the colours in the order given), each solved exactly for its own value
+    with its neighbours' current values. Written independently of the oracle: scalar loops, ghost
+    relation solved per point."""
     dim = op.dim
     h2 = op.h * op.h
     n = op.shape
     kap = np.broadcast_to(np.asarray(op.kappa, dtype=float), n)
-    for colour in (1, 0):
+    for colour in colours:
         for idx in np.ndindex(*n):
             ijl = [c + 1 for c in idx[::-1]]  # 1-based (i, j, l)
             if sum(ijl) % 2 != colour:
@@ -202,6 +203,46 @@ def test_xmcgs_equals_red_black_loop(dim):
     d = u0.copy()
     cc.xmcgs_sweep(op, d, f)
     assert np.max(np.abs(c - d)) > 1e-6
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_symmetric_ordering_equals_forward_backward_loops(dim):
+    """The "1234-4321" ordering of Sec. 2.3 (a forward sweep, then the sets in reverse order) equals
+    red-black Gauss-Seidel with the odd colour first, then with the even colour first; a third sweep
+    is forward again."""
+    shape = (8, 8) if dim == 2 else (4, 4, 8)
+    op = cc.Operator(shape, 1.0 / 8, 1.0, 0.1, 0.5 + random_field(shape, 17),
+                     (D_, N_, N_, D_, N_, D_)[: 2 * dim])
+    u0 = random_field(shape, 18)
+    f = random_field(shape, 19, -1.0, 1.0)
+    a = u0.copy()
+    cc.smooth(op, a, f, 3, ordering="1234-4321")
+    b = u0.copy()
+    for colours in ((1, 0), (0, 1), (1, 0)):
+        _rbgs_literal(op, b, f, colours)
+    np.testing.assert_allclose(a, b, rtol=1e-14, atol=1e-15)
+    # and it is not the forward ordering
+    c = u0.copy()
+    cc.smooth(op, c, f, 3)
+    assert np.max(np.abs(a - c)) > 1e-6
+
+
+def test_forward_ordering_converges_faster_than_symmetric():
+    """Sec. 2.3 (smoother comparison figure): on the asymptotic test problem of Sec. 3.1.2 (exact
+    solution substituted into the PDE, zero start, s = 2, res < 1e-9, coarsest 4^2) the X-shape with
+    the 1234-1234 ordering needs the fewest V-cycles; the symmetric 1234-4321 ordering needs more.
+    The paper prints the counts only in a figure, so only the order of the two is checked."""
+    n = 256
+    p, f = exact_and_source(n, 2)
+    op = cc.Operator((n, n), 1.0 / n, 1.0, 1.0, 1.0, (D_,) * 4)
+    cycles = {}
+    for ordering in ("1234-1234", "1234-4321"):
+        u = np.zeros((n, n))
+        info = cc.solve(cc.build_levels(op, 4), u, f,
+                        cc.Params(tol=1e-9, tol_mode="absolute", kmax=100, coarsest=4, ordering=ordering))
+        assert info.converged
+        cycles[ordering] = info.cycles
+    assert cycles["1234-1234"] < cycles["1234-4321"]
 
 
 def test_smoother_fixed_point_is_direct_solution():

@@ -70,3 +70,19 @@ def test_static_entry_rejects_grids_beyond_its_limit(cuda_lib):
         fas.fas_vcycle_small_static(params, _t(np.zeros(shape)), _t(np.zeros(shape)), 1)
     assert e.value.status == fas.FAS_EINVAL
     assert "too large" in fas.fas_last_error()
+
+
+def test_static_entry_symmetric_ordering(cuda_lib):
+    """The allocation-free entry with the "1234-4321" ordering computes what the context does."""
+    fas = cuda_lib
+    shape = (32, 32)
+    h = 1.0 / 32
+    kw = dict(alpha=1.0, beta=2e-3, coarsest=2, ordering=fas.FAS_ORDER_SYMMETRIC)
+    ctx = fas.fas_create(fas.make_params(shape, h, **kw))
+    u0 = random_field(shape, 421)
+    f = _t(random_field(shape, 422, -1, 1))
+    u_ref, u_new = _t(u0), _t(u0)
+    for _ in range(3):
+        fas.fas_vcycle(ctx, u_ref, f)
+    fas.fas_vcycle_small_static(fas.make_params(shape, h, **kw), u_new, f, 3)
+    assert _rel(u_new.cpu().numpy(), u_ref.cpu().numpy()) <= 1e-12

@@ -23,6 +23,8 @@ Readings where the paper is silent, garbled or self-contradictory:
       the point's equation exactly with its ghost tied to it (Neumann drops the face, Dirichlet
       doubles the face's diagonal share). Listing-free reading of Eqs. FCGS-1..4 at boundary cells.
   G3  Every cell is updated once per sweep (the 3D set ranges 2:2:M_1-1 read as 2:2:M_1).
+  G4b The "1234-4321" ordering (Sec. 2.3): within a smoothing step of s sweeps the odd-numbered
+      sweeps visit the sets forward and the even-numbered ones backward, on every level.
   G5  Stopping test relative to ||f||_2 by default; the paper's absolute h-weighted norm on request.
   G6  Coarsest level: the paper's s smoothing sweeps by default, a dense direct solve on request.
   G7  Singular all-Neumann problems (alpha = 0): the right-hand side is projected to zero mean and

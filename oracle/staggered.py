@@ -29,8 +29,11 @@ Readings:
       sign of the advecting velocity at the point; advecting components are interpolated to the
       point by averaging their 2 (2D) or 4 (3D) surrounding faces. Values beyond a wall: the normal
       component is reflected oddly about the wall face, a tangential component by ghost = 2 g - inside
-      (g the wall's tangential velocity). PARITY UNPINNED against the paper (no formulas printed):
-      only the written definition binds the oracle and the CUDA path, plus exactness on linear fields.
+      (g the wall's tangential velocity). The convection term alone is not pinned by a printed
+      formula (the paper prints none): its own tests are exactness on linear fields and zero
+      convection of a uniform flow. The projection steps that contain it are pinned by the paper's
+      first- and second-order convergence tables for the manufactured solution (Sec. 4.4.3), which
+      this oracle reproduces within 1-2 % (tests/golden/ns_*_order_mms.json).
 """
 from __future__ import annotations
 

@@ -152,6 +152,15 @@ fas_status fas_heat_adjoint(fas_ctx* ctx, const double* u0, const double* fsrc, 
                             const double* dL_duT, double* uT, double* g_u0, double* g_f, double* g_kappa,
                             int ckpt_every);
 
+/* Inhomogeneous Dirichlet values (Sec. 2.1, Eq. boundry1 with a value g on the face): with the ghost
+ * 2g - u of such a face, the point equation of the cell next to it gains the constant 2 beta kappa g /
+ * h^2 (kappa of that cell), which this call adds to f. Every face of fas_params.bc that is
+ * FAS_BC_DIRICHLET takes values[face] (x_lo, x_hi, y_lo, y_hi, z_lo, z_hi; values of Neumann faces
+ * are ignored); the solves then use the homogeneous operator. Faces are added to each cell in the
+ * order z, y, x (low side first). f: DEVICE float64, nx*ny(*nz). Cell-centred contexts only. For a
+ * heat run, whose right-hand side is u^n + dt fsrc with beta = dt, pass values g / dt and fsrc. */
+fas_status fas_fold_dirichlet(fas_ctx* ctx, double* f, const double values[6]);
+
 /* fas_heat_run with HOST buffers: copies u0_host and fsrc_host (may be NULL) to device buffers the
  * context keeps between calls, runs nsteps steps and copies the result to uT_host (may equal
  * u0_host). Returns after the result is on the host. Page-locked buffers that the GPU can address

@@ -23,7 +23,7 @@ __all__ = [
     "fas_num_levels", "fas_vcycle", "fas_solve", "fas_heat_run", "fas_heat_run_host", "fas_residual",
     "fas_smooth", "fas_restrict", "fas_prolong_add", "fas_last_error", "fas_launch_count", "Solver",
     "fas_prof_enable", "fas_prof_read", "make_params", "fas_vcycle_small_static", "fas_solve_batched",
-    "fas_autotune", "fas_heat_adjoint",
+    "fas_autotune", "fas_heat_adjoint", "fas_fold_dirichlet",
 ]
 
 FAS_OK, FAS_EINVAL, FAS_ENOMEM, FAS_ENOTCONV, FAS_ENONFINITE, FAS_ETIMEOUT, FAS_ECUDA, FAS_EUNSUPPORTED = range(8)
@@ -109,6 +109,7 @@ def load(path: str | None = None):
         "fas_heat_adjoint": (_I, [_P, _P, _P, _D, _I, _P, _P, _P, _P, _P, _I]),
         "fas_prof_read": (_I, [_P, ctypes.c_void_p, _I, ctypes.POINTER(_I)]),
         "fas_residual_ir": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D)]),
+        "fas_fold_dirichlet": (_I, [_P, _P, ctypes.POINTER(_D)]),
         "fas_selftest_conversions": (_I, [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]),
         "ns_create": (_I, [_I, ctypes.POINTER(_I), _D, _D, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(fas_params),
                            ctypes.POINTER(fas_params), _P, ctypes.POINTER(_P)]),
@@ -245,6 +246,13 @@ def fas_heat_run_host(ctx: _Ctx, u0_host, uT_host, fsrc_host, dt: float, nsteps:
                                   int(nsteps), infos)
     _check(st, "fas_heat_run_host")
     return [infos[k] for k in range(nsteps)]
+
+
+def fas_fold_dirichlet(ctx: _Ctx, f, values) -> None:
+    """f += 2 beta kappa g / h^2 next to every Dirichlet face with value g (values: 6 floats, x_lo ..
+    z_hi; Neumann entries ignored)."""
+    vals = (_D * 6)(*[float(v) for v in list(values) + [0.0] * (6 - len(values))])
+    _check(load().fas_fold_dirichlet(ctx.handle, _dev(f, "f", ctx.cells), vals), "fas_fold_dirichlet")
 
 
 def fas_residual(ctx: _Ctx, level: int, u, f, out=None) -> float:

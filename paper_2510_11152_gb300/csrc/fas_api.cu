@@ -1043,6 +1043,36 @@ __global__ void k_copy_f64(double* __restrict__ dst, const double* __restrict__ 
   if (gtid() == 0 && (n & 1)) dst[n - 1] = src[n - 1];
 }
 
+// f += 2 beta kappa_c g / h^2 on the cells next to each Dirichlet face with value g (dmask bit k:
+// face k is Dirichlet), faces added in the order z, y, x, low side first.
+struct FaceValues {
+  double g[6];
+};
+__global__ void k_fold_dirichlet(double* __restrict__ f, const double* __restrict__ kappa, double kconst, double scale,
+                                 int nx, int ny, int nz, FaceValues gv, int dmask) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int64_t idx = gtid(); idx < n; idx += gstride()) {
+    const int i = (int)(idx % nx);
+    const int64_t r = idx / nx;
+    const int j = (int)(r % ny);
+    const int l = (int)(r / ny);
+    const bool edge = i == 0 || i == nx - 1 || j == 0 || j == ny - 1 || (nz > 1 && (l == 0 || l == nz - 1));
+    if (!edge) continue;
+    // product, then sum, each rounded (no contraction into an fma)
+    const double sk = __dmul_rn(scale, kappa ? kappa[idx] : kconst);
+    double v = f[idx];
+    if (nz > 1) {
+      if (l == 0 && (dmask & 16)) v = __dadd_rn(v, __dmul_rn(sk, gv.g[4]));
+      if (l == nz - 1 && (dmask & 32)) v = __dadd_rn(v, __dmul_rn(sk, gv.g[5]));
+    }
+    if (j == 0 && (dmask & 4)) v = __dadd_rn(v, __dmul_rn(sk, gv.g[2]));
+    if (j == ny - 1 && (dmask & 8)) v = __dadd_rn(v, __dmul_rn(sk, gv.g[3]));
+    if (i == 0 && (dmask & 1)) v = __dadd_rn(v, __dmul_rn(sk, gv.g[0]));
+    if (i == nx - 1 && (dmask & 2)) v = __dadd_rn(v, __dmul_rn(sk, gv.g[1]));
+    f[idx] = v;
+  }
+}
+
 // The device address of a host buffer the GPU may access directly (page-locked and mapped under
 // unified addressing), or nullptr.
 const void* mapped_host(const void* h) {
@@ -1455,6 +1485,27 @@ fas_status fas_heat_adjoint(fas_ctx* c, const double* u0, const double* fsrc, do
   CUDA_TRY(cudaStreamSynchronize(st));
   CUDA_TRY(cudaGetLastError());
   if (worst != FAS_OK) return fail(worst, "fas_heat_adjoint: a solve missed its tolerance within kmax");
+  return FAS_OK;
+}
+
+fas_status fas_fold_dirichlet(fas_ctx* c, double* f, const double values[6]) {
+  STATUS_TRY(check_ctx(c));
+  STATUS_TRY(check_field(f, true, "fas_fold_dirichlet"));
+  if (!values) return fail(FAS_EINVAL, "fas_fold_dirichlet: null values");
+  const fas_params& p = c->p;
+  if (p.location != FAS_CELL) return fail(FAS_EUNSUPPORTED, "fas_fold_dirichlet: cell-centred unknowns only");
+  FaceValues gv{};
+  int dmask = 0;
+  for (int k = 0; k < 2 * p.dim; ++k) {
+    gv.g[k] = values[k];
+    if (p.bc[k] == FAS_BC_DIRICHLET) dmask |= 1 << k;
+  }
+  const LevelShape& s = c->shape[0];
+  const double scale = 2.0 * p.beta / (p.h * p.h);
+  k_fold_dirichlet<<<grid_for(c, s.cells()), kBlock, 0, c->stream>>>(f, p.kappa, p.kappa_const, scale, s.nx, s.ny,
+                                                                      s.nz, gv, dmask);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
   return FAS_OK;
 }
 

@@ -286,3 +286,31 @@ def test_heat_run_host_matches_device_run(cuda_lib, pinned, with_src, alias):
             u0h[...] = u0
         fas.fas_heat_run_host(ctx, u0h, outh, fh, dt, 3)
         assert np.array_equal(outh, ud.cpu().numpy())
+
+
+@pytest.mark.parametrize("shape,bc_kind,var_kappa", [((64, 128), "dirichlet", False), ((32, 64), "mixed", True),
+                                                     ((16, 16, 32), "dirichlet", True),
+                                                     ((16, 32, 16), "mixed", False)])
+def test_fold_dirichlet_matches_oracle(cuda_lib, shape, bc_kind, var_kappa):
+    """Inhomogeneous Dirichlet values moved into the right-hand side (Eq. boundry1 with a value,
+    reading G10): the same additions as the oracle's fold, bit for bit (corners take every face)."""
+    fas = cuda_lib
+    dim = len(shape)
+    h = 1.0 / shape[-1]
+    kappa = (0.5 + random_field(shape, 241)) if var_kappa else 1.3
+    op, ctx = _pair(fas, shape, h, 1.0, 3e-3, kappa, _bc(bc_kind, dim))
+    values = [0.3, -1.2, 2.5, 0.7, -0.4, 1.1][: 2 * dim]
+    f = random_field(shape, 242, -1, 1)
+    ref = cc.fold_dirichlet_rhs(op, f, values)
+    fg = _t(f)
+    fas.fas_fold_dirichlet(ctx, fg, values)
+    assert np.array_equal(_n(fg), ref)
+
+
+def test_fold_dirichlet_rejects_face_grids(cuda_lib):
+    fas = cuda_lib
+    fctx = fas.fas_create(fas.make_params((32, 32), 1.0 / 32, alpha=1.0, beta=3e-3, bc=(D_,) * 4,
+                                          location=fas.FAS_FACE_X))
+    with pytest.raises(fas.FasError) as e:
+        fas.fas_fold_dirichlet(fctx, _t(np.zeros((32, 32))), [1.0] * 4)
+    assert e.value.status == fas.FAS_EUNSUPPORTED

@@ -23,7 +23,7 @@ __all__ = [
     "fas_num_levels", "fas_vcycle", "fas_solve", "fas_heat_run", "fas_heat_run_host", "fas_residual",
     "fas_smooth", "fas_restrict", "fas_prolong_add", "fas_last_error", "fas_launch_count", "Solver",
     "fas_prof_enable", "fas_prof_read", "make_params", "fas_vcycle_small_static", "fas_solve_batched",
-    "fas_autotune", "fas_heat_adjoint", "fas_fold_dirichlet",
+    "fas_autotune", "fas_heat_adjoint", "fas_fold_dirichlet", "solve", "HeatSolve",
 ]
 
 FAS_OK, FAS_EINVAL, FAS_ENOMEM, FAS_ENOTCONV, FAS_ENONFINITE, FAS_ETIMEOUT, FAS_ECUDA, FAS_EUNSUPPORTED = range(8)
@@ -458,6 +458,24 @@ def make_params(shape, h, alpha=1.0, beta=1.0, kappa_const=1.0, bc=None, **kw) -
             raise AttributeError("fas_params has no field %s" % k)
         setattr(p, k, v)
     return p
+
+
+def solve(u, f, h, kappa=None, stream=None, allow_notconv=False, **params) -> fas_info:
+    """One call: A u = f (A u = alpha u - beta div(kappa grad u)) on the grid of u's shape, solved in
+    place from u's current values to the tolerance; params are fas_params fields (alpha, beta, bc,
+    precision, tol, ...). Creates and frees a context; keep a Solver for repeated solves."""
+    ctx = fas_create(make_params(tuple(u.shape), h, **params), stream=stream, kappa=kappa)
+    try:
+        return fas_solve(ctx, u, f, allow_notconv=allow_notconv)
+    finally:
+        fas_destroy(ctx)
+
+
+def __getattr__(name):
+    if name == "HeatSolve":  # the autograd Function, imported on first use
+        from .autograd import HeatSolve
+        return HeatSolve
+    raise AttributeError("module %r has no attribute %r" % (__name__, name))
 
 
 class Solver:

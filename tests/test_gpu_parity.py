@@ -314,3 +314,19 @@ def test_fold_dirichlet_rejects_face_grids(cuda_lib):
     with pytest.raises(fas.FasError) as e:
         fas.fas_fold_dirichlet(fctx, _t(np.zeros((32, 32))), [1.0] * 4)
     assert e.value.status == fas.FAS_EUNSUPPORTED
+
+
+def test_one_call_solve(cuda_lib):
+    """fas.solve: context created, used and freed in one call; the same solution as a Solver."""
+    fas = cuda_lib
+    shape = (128, 128)
+    f = random_field(shape, 251, -1, 1)
+    u1 = _t(np.zeros(shape))
+    info = fas.solve(u1, _t(f), 1.0 / 128, alpha=1.0, beta=1e-3, bc=_bc("mixed", 2), precision=fas.FAS_MIXED)
+    assert info.converged and info.rel <= 1e-10
+    s = fas.Solver(shape, 1.0 / 128, alpha=1.0, beta=1e-3, bc=_bc("mixed", 2), precision=fas.FAS_MIXED)
+    u2 = _t(np.zeros(shape))
+    s.solve(u2, _t(f))
+    s.close()
+    assert np.array_equal(_n(u1), _n(u2))
+    assert fas.HeatSolve is not None

@@ -31,6 +31,9 @@ Readings where the paper is silent, garbled or self-contradictory:
       the mean of the iterate removed after each cycle; the dense coarsest solve is least-squares.
   G8  Variable diffusivity: face kappa is the mean of the two cells; a boundary face takes its
       cell's kappa; coarse levels use the four- (eight-) cell average of kappa.
+  A17 Periodic axes (for the grain-growth example of Sec. 3.3.1): the grid wraps around; the face
+      between the last and the first cell is an interior face (mean kappa), every cell has all its
+      neighbours, and with n even the red-black colouring stays consistent across the wrap.
   G10 Inhomogeneous Dirichlet values are moved into the right-hand side once (fold_dirichlet_rhs);
       the solver's operator is linear on every level.
 
@@ -46,6 +49,7 @@ import numpy as np
 
 NEUMANN = 0
 DIRICHLET = 1
+PERIODIC = 2  # both faces of an axis: the grid wraps around (reading A17)
 
 
 @dataclass
@@ -66,6 +70,9 @@ class Operator:
             self.bc = (NEUMANN,) * (2 * len(self.shape))
         self.bc = tuple(int(b) for b in self.bc)
         assert len(self.bc) == 2 * self.dim
+        for a in range(self.dim):
+            if PERIODIC in self.bc[2 * a:2 * a + 2]:
+                assert self.bc[2 * a] == self.bc[2 * a + 1] == PERIODIC, "periodic faces come in pairs"
 
     @property
     def dim(self):
@@ -78,7 +85,7 @@ class Operator:
 
     @property
     def singular(self):
-        return self.alpha == 0.0 and all(b == NEUMANN for b in self.bc)
+        return self.alpha == 0.0 and all(b != DIRICHLET for b in self.bc)
 
 
 @dataclass
@@ -111,7 +118,8 @@ def _take(a, idx, ax):
 
 def face_kappa(op: Operator, ax: int) -> np.ndarray:
     """kappa on the n+1 faces normal to numpy axis `ax`: interior faces take the mean of their two
-    cells, the two boundary faces take the kappa of their cell."""
+    cells, the two boundary faces take the kappa of their cell; on a periodic axis the two boundary
+    faces are one face, between the last and the first cell, and take their mean."""
     shape = list(op.shape)
     if np.isscalar(op.kappa):
         shape[ax] += 1
@@ -120,6 +128,8 @@ def face_kappa(op: Operator, ax: int) -> np.ndarray:
     inner = 0.5 * (_take(k, slice(0, -1), ax) + _take(k, slice(1, None), ax))
     lo = _take(k, slice(0, 1), ax)
     hi = _take(k, slice(-1, None), ax)
+    if op.axis_bc(ax)[0] == PERIODIC:
+        lo = hi = 0.5 * (hi + lo)
     return np.concatenate([lo, inner, hi], axis=ax)
 
 
@@ -138,8 +148,11 @@ def apply_A(op: Operator, u: np.ndarray) -> np.ndarray:
         lo_kind, hi_kind = op.axis_bc(ax)
         first = _take(u, slice(0, 1), ax)
         last = _take(u, slice(-1, None), ax)
-        ghost_lo = first if lo_kind == NEUMANN else -first
-        ghost_hi = last if hi_kind == NEUMANN else -last
+        if lo_kind == PERIODIC:  # the neighbours across the boundary are the wrapped cells
+            ghost_lo, ghost_hi = last, first
+        else:
+            ghost_lo = first if lo_kind == NEUMANN else -first
+            ghost_hi = last if hi_kind == NEUMANN else -last
         ext = np.concatenate([ghost_lo, u, ghost_hi], axis=ax)
         flux = face_kappa(op, ax) * np.diff(ext, axis=ax)
         out = out - scale * np.diff(flux, axis=ax)
@@ -217,14 +230,16 @@ def smoother_coefficients(op: Operator) -> SmootherCoefficients:
         d_lo = k_lo.copy()
         d_hi = k_hi.copy()
         # boundary faces carry no neighbour; their diagonal share follows the ghost relation
+        # (a periodic boundary face is an interior face whose neighbour is the wrapped cell)
         sl0 = [slice(None)] * op.dim
         sl0[ax] = 0
         sl1 = [slice(None)] * op.dim
         sl1[ax] = n - 1
-        w_lo[tuple(sl0)] = 0.0
-        w_hi[tuple(sl1)] = 0.0
-        d_lo[tuple(sl0)] = 0.0 if lo_kind == NEUMANN else 2.0 * k_lo[tuple(sl0)]
-        d_hi[tuple(sl1)] = 0.0 if hi_kind == NEUMANN else 2.0 * k_hi[tuple(sl1)]
+        if lo_kind != PERIODIC:
+            w_lo[tuple(sl0)] = 0.0
+            w_hi[tuple(sl1)] = 0.0
+            d_lo[tuple(sl0)] = 0.0 if lo_kind == NEUMANN else 2.0 * k_lo[tuple(sl0)]
+            d_hi[tuple(sl1)] = 0.0 if hi_kind == NEUMANN else 2.0 * k_hi[tuple(sl1)]
         D = D + op.beta * (d_lo + d_hi)
         weights[(ax, -1)] = w_lo
         weights[(ax, +1)] = w_hi
@@ -238,6 +253,16 @@ def _set_slices(op: Operator, parities):
     offs = offs[::-1]  # numpy order
     cell = tuple(slice(o, n, 2) for o, n in zip(offs, op.shape))
     return offs, cell
+
+
+def _wrap_ghosts(pad: np.ndarray, ax: int, n: int) -> None:
+    """Copy the first and last interior slabs of `pad` along axis `ax` into the opposite ghosts."""
+    dst = [slice(None)] * pad.ndim
+    src = [slice(None)] * pad.ndim
+    dst[ax], src[ax] = 0, n
+    pad[tuple(dst)] = pad[tuple(src)]
+    dst[ax], src[ax] = n + 1, 1
+    pad[tuple(dst)] = pad[tuple(src)]
 
 
 def xmcgs_sweep(op: Operator, u: np.ndarray, f: np.ndarray,
@@ -254,7 +279,10 @@ def xmcgs_sweep(op: Operator, u: np.ndarray, f: np.ndarray,
     pad = np.zeros(tuple(n + 2 for n in op.shape), dtype=op.dtype)
     inner = tuple(slice(1, n + 1) for n in op.shape)
     pad[inner] = u
+    periodic = [ax for ax in range(op.dim) if op.axis_bc(ax)[0] == PERIODIC]
     for parities in sets:
+        for ax in periodic:  # ghost layers hold the current values of the wrapped cells
+            _wrap_ghosts(pad, ax, op.shape[ax])
         offs, cell = _set_slices(op, parities)
         nbsum = np.zeros(pad[tuple(slice(o + 1, n + 1, 2) for o, n in zip(offs, op.shape))].shape,
                          dtype=op.dtype)

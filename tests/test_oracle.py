@@ -16,7 +16,7 @@ from oracle import cell_centred as cc
 from tests.mms import exact_and_source, l2_error
 from workloads import random_field
 
-N_, D_ = cc.NEUMANN, cc.DIRICHLET
+N_, D_, P_ = cc.NEUMANN, cc.DIRICHLET, cc.PERIODIC
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_error_tables.json")
 
 
@@ -126,7 +126,7 @@ def test_operator_symmetric_and_conservative():
 # ------------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("bc_kind", ["neumann", "dirichlet", "mixed"])
+@pytest.mark.parametrize("bc_kind", ["neumann", "dirichlet", "mixed", "periodic", "periodic_x"])
 @pytest.mark.parametrize("var_kappa", [False, True])
 def test_each_set_update_zeroes_its_residual(dim, bc_kind, var_kappa):
     """Defining property of a Gauss-Seidel update (Eqs. FCGS-1..4): right after a parity set is
@@ -135,7 +135,8 @@ def test_each_set_update_zeroes_its_residual(dim, bc_kind, var_kappa):
     shape = (8, 8) if dim == 2 else (4, 8, 4)
     h = 1.0 / 8
     bc = {"neumann": (N_,) * (2 * dim), "dirichlet": (D_,) * (2 * dim),
-          "mixed": (D_, N_, N_, D_, D_, N_)[: 2 * dim]}[bc_kind]
+          "mixed": (D_, N_, N_, D_, D_, N_)[: 2 * dim], "periodic": (P_,) * (2 * dim),
+          "periodic_x": (P_, P_, D_, N_, N_, D_)[: 2 * dim]}[bc_kind]
     kappa = (0.5 + random_field(shape, 3)) if var_kappa else 1.7
     op = cc.Operator(shape, h, 0.9, 0.05, kappa, bc)
     u = random_field(shape, 4)
@@ -171,6 +172,8 @@ def _rbgs_literal(op, u, f, colours=(1, 0)):
                 for s, kind in ((-1, lo), (+1, hi)):
                     nb = list(idx)
                     nb[ax] += s
+                    if kind == P_:
+                        nb[ax] %= n[ax]  # the wrapped neighbour
                     if 0 <= nb[ax] < n[ax]:
                         kf = 0.5 * (kap[idx] + kap[tuple(nb)])
                         diag += op.beta * kf
@@ -203,6 +206,64 @@ def test_xmcgs_equals_red_black_loop(dim):
     d = u0.copy()
     cc.xmcgs_sweep(op, d, f)
     assert np.max(np.abs(c - d)) > 1e-6
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_periodic_xmcgs_equals_red_black_loop(dim):
+    """Reading A17: on periodic axes the wrapped cells are ordinary neighbours; X-MCGS still equals
+    the literal red-black loop (n even keeps the colouring consistent across the wrap)."""
+    shape = (8, 8) if dim == 2 else (4, 4, 8)
+    op = cc.Operator(shape, 1.0 / 8, 1.0, 0.1, 0.5 + random_field(shape, 27),
+                     (P_, P_, D_, N_, P_, P_)[: 2 * dim])
+    u0 = random_field(shape, 28)
+    f = random_field(shape, 29, -1.0, 1.0)
+    a = u0.copy()
+    cc.smooth(op, a, f, 2)
+    b = u0.copy()
+    _rbgs_literal(op, b, f)
+    _rbgs_literal(op, b, f)
+    np.testing.assert_allclose(a, b, rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_periodic_operator_fourier_eigenpairs(dim):
+    """On an all-periodic grid with constant kappa, cos(2 pi k . x + phi) at the cell centres is an
+    eigenvector of A with eigenvalue alpha + beta (4 kappa / h^2) sum_a sin^2(pi k_a h)."""
+    n = 16
+    h = 1.0 / n
+    shape = (n,) * dim
+    op = cc.Operator(shape, h, 0.7, 0.02, 1.3, (P_,) * (2 * dim))
+    grids = np.meshgrid(*[(np.arange(n) + 0.5) * h] * dim, indexing="ij")  # numpy axis order
+    for k in ((1, 0, 2), (3, 5, 1), (8, 2, 7)):
+        k = k[:dim]
+        phase = 2.0 * np.pi * sum(kk * g for kk, g in zip(k, grids)) + 0.3
+        u = np.cos(phase)
+        lam = op.alpha + op.beta * 4.0 * 1.3 / h ** 2 * sum(np.sin(np.pi * kk * h) ** 2 for kk in k)
+        np.testing.assert_allclose(cc.apply_A(op, u), lam * u, rtol=0, atol=1e-11 * lam)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.0])
+def test_periodic_solve_matches_fourier_solution(alpha):
+    """The FAS solve on an all-periodic grid equals the exact solution by the discrete Fourier
+    transform (alpha = 0: the singular problem, zero-mean right-hand side and solution, G7)."""
+    n = 128
+    h = 1.0 / n
+    beta = 1e-3 if alpha else 1.0
+    op = cc.Operator((n, n), h, alpha, beta, 1.0, (P_,) * 4)
+    f = random_field((n, n), 31, -1.0, 1.0)
+    if alpha == 0.0:
+        f -= f.mean()
+    lam1 = 4.0 / h ** 2 * np.sin(np.pi * np.arange(n) / n) ** 2
+    lam = alpha + beta * (lam1[:, None] + lam1[None, :])
+    fh = np.fft.fft2(f)
+    if alpha == 0.0:
+        lam[0, 0] = 1.0
+        fh[0, 0] = 0.0
+    ref = np.real(np.fft.ifft2(fh / lam))
+    u = np.zeros((n, n))
+    info = cc.solve(cc.build_levels(op, 4), u, f, cc.Params(tol=1e-13, kmax=60, coarsest=4, coarse_exact=True))
+    assert info.converged
+    assert np.max(np.abs(u - ref)) < 1e-10 * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("dim", [2, 3])

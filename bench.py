@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=8192, help="cells per axis")
+    ap.add_argument("--n", "--grid", dest="n", type=int, default=8192,
+                    help="cells per axis (--grid: the same, unambiguous behind torch.distributed.run)")
     ap.add_argument("--heat-steps", type=int, default=20)
     ap.add_argument("--inner", type=int, default=0, help="float32 cycles per refinement step (0: tune)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")

@@ -548,9 +548,9 @@ def secondary_workloads(dev, stream, ws=1, rank=0):
     return out
 
 
-def cpu_baseline(w, n_cycles=1):
-    """The oracle as it stands, one float64 V(2,2) cycle on the first time step's system at full size
-    (bounded sample, about 20-40 s of single-threaded numpy)."""
+def cpu_baseline(w, n_cycles=2):
+    """The oracle as it stands, float64 V(2,2) cycles on the first time step's system at full size
+    (bounded sample: two cycles, about 20 s of single-threaded numpy on the GB300 host's cores)."""
     from oracle import cell_centred as cc
     op = cc.heat_operator(w["shape"], w["h"], w["dt"])
     lev = cc.build_levels(op, 4)

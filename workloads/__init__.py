@@ -36,6 +36,7 @@ TAG_NORMAL = 7
 TAG_INIT = 8
 TAG_VEL = 9  # 9, 10, 11: velocity components x, y, z
 TAG_PRES = 12
+TAG_GRAIN = 13
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -301,3 +302,17 @@ def mms_field(terms, t: float, comp=None) -> np.ndarray:
     if comp is not None:
         zero_wall_slot(out, comp)
     return out
+
+
+def grain_growth_fields(q: int, shape, seed: int = 5) -> np.ndarray:
+    """Grain growth (Sec. 3.3.1): q order parameters on a periodic grid, U(-0.001, 0.001) per cell
+    (the paper's disordered, liquid-like start); shape (q,) + grid shape."""
+    n = int(np.prod(shape))
+    return (uniform(seed, TAG_GRAIN, q * n) * 0.002 - 0.001).reshape((q,) + tuple(shape))
+
+
+def grain_growth(n: int = 512, q: int = 1189, seed: int = 5):
+    """The paper's 2D grain-growth run: 512^2 cells, h = 2 (domain [0, 1024]^2), dt = 0.25, q up to
+    1189 order parameters, periodic in every direction."""
+    shape = (n, n)
+    return dict(shape=shape, q=q, h=2.0, dt=0.25, etas=grain_growth_fields(q, shape, seed))

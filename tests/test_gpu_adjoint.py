@@ -28,25 +28,32 @@ def _case(n, seed):
                 target=random_field(shape, seed + 3, -1, 1))
 
 
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
 @pytest.mark.parametrize("bc", [(N_,) * 4, (D_, N_, N_, D_)])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_adjoint_matches_oracle(cuda_lib, bc, precision):
+    """The final state and the three gradients against the oracle's adjoint within 1e-10 relative
+    max-norm, every solve on both sides taken to 1e-13 relative residual (the gradients are sums
+    over steps of products of solved fields, so the comparison needs solves well past the bar)."""
     fas = cuda_lib
     c = _case(64, 701)
     dt, steps = 2e-3, 6
-    prm = cc.Params(tol=1e-12, kmax=60, coarsest=4)
+    prm = cc.Params(tol=1e-13, kmax=80, coarsest=4)
     op = cc.Operator(c["shape"], c["h"], 1.0, dt, c["kappa"], bc)
     uT_ref, _ = cc.heat_run(op, c["u0"], c["f"], dt, steps, prm)
     seed = 2.0 * (uT_ref - c["target"])
     _, gu_ref, gf_ref, gk_ref = cc.adjoint_heat(op, c["u0"], c["f"], dt, steps, seed, prm)
-    ctx = fas.fas_create(fas.make_params(c["shape"], c["h"], beta=dt, bc=bc, coarsest=4, tol=1e-12, kmax=60,
+    ctx = fas.fas_create(fas.make_params(c["shape"], c["h"], beta=dt, bc=bc, coarsest=4, tol=1e-13, kmax=80,
                                          precision=precision), kappa=_t(c["kappa"]))
     outs = [_t(np.zeros(c["shape"])) for _ in range(4)]
     fas.fas_heat_adjoint(ctx, _t(c["u0"]), _t(c["f"]), dt, steps, _t(seed), *outs, ckpt_every=4)
     uT, gu, gf, gk = (o.cpu().numpy() for o in outs)
-    assert _rel2(uT, uT_ref) <= 1e-10
-    for g, ref in ((gu, gu_ref), (gf, gf_ref), (gk, gk_ref)):
-        assert _rel2(g, ref) <= 1e-9
+    assert _rel(uT, uT_ref) <= 1e-10, _rel(uT, uT_ref)
+    for name, g, ref in (("u0", gu, gu_ref), ("f", gf, gf_ref), ("kappa", gk, gk_ref)):
+        assert _rel(g, ref) <= 1e-10, (name, _rel(g, ref))
 
 
 def test_checkpoint_interval_does_not_change_gradients(cuda_lib):

@@ -25,17 +25,21 @@ def _ctx(fas, pr, **kw):
                                           coarsest=4, precision=1, **kw))
 
 
-def test_batched_equals_one_at_a_time_and_oracle(cuda_lib):
+@pytest.mark.parametrize("tol", [1e-10, 1e-12])
+def test_batched_equals_one_at_a_time_and_oracle(cuda_lib, tol):
+    """Batched = one at a time bit for bit; each result against the oracle's solution to 1e-13:
+    solved to the workload's 1e-10, within 1e-10 relative in the 2-norm (the norm a 1e-10 relative
+    residual bounds); solved to 1e-12, within 1e-10 relative max-norm."""
     fas = cuda_lib
     probs = _problems(10, (64, 128, 256))
     fs = [batched_problem_rhs(p) for p in probs]
-    ctxs = [_ctx(fas, p) for p in probs]
+    ctxs = [_ctx(fas, p, tol=tol, kmax=40) for p in probs]
     us = [_t(np.zeros((p["n"], p["n"]))) for p in probs]
     infos = fas.fas_solve_batched(ctxs, us, [_t(f) for f in fs])
-    assert all(i.converged and i.rel <= 1e-10 for i in infos)
+    assert all(i.converged and i.rel <= tol for i in infos)
     for p, f, u, inf in zip(probs, fs, us, infos):
         n = p["n"]
-        ctx1 = _ctx(fas, p)
+        ctx1 = _ctx(fas, p, tol=tol, kmax=40)
         u1 = _t(np.zeros((n, n)))
         inf1 = fas.fas_solve(ctx1, u1, _t(f))
         np.testing.assert_array_equal(u.cpu().numpy(), u1.cpu().numpy())
@@ -43,9 +47,11 @@ def test_batched_equals_one_at_a_time_and_oracle(cuda_lib):
         op = cc.Operator((n, n), 1.0 / n, 1.0, p["dt"], p["kappa"])
         ref = np.zeros((n, n))
         cc.solve(cc.build_levels(op, 4), ref, f, cc.Params(tol=1e-13, kmax=60, coarsest=4))
-        # the tolerance bounds the residual in the 2-norm; the solution is compared in that norm
         ug = u.cpu().numpy()
-        assert np.linalg.norm(ug - ref) <= 1e-10 * np.linalg.norm(ref)
+        if tol >= 1e-10:
+            assert np.linalg.norm(ug - ref) <= 1e-10 * np.linalg.norm(ref)
+        else:
+            assert np.max(np.abs(ug - ref)) <= 1e-10 * np.max(np.abs(ref))
 
 
 def test_batched_graph_reuse_and_errors(cuda_lib):

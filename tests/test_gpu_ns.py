@@ -119,10 +119,16 @@ def test_face_converged_solution(cuda_lib, precision, shape, comp):
     if precision == 0:
         assert info.cycles == info_ref.cycles
         assert _rel(_n(ug), u_ref) <= 1e-12
-    else:
-        assert _rel2(_n(ug), u_ref) <= 1e-10
     r = st.residual_face(op, _n(ug), f)
     assert cc.norm2(r) <= 1e-10 * cc.norm2(f) * (1 + 1e-6)
+    # against the oracle's solution to 1e-13, within 1e-10 relative max-norm: the GPU side solved
+    # to 1e-12 (a 1e-10 residual bounds the error only in the 2-norm)
+    _, ctx_t = _face_pair(fas, shape, comp, beta, coarsest=4, precision=precision, kmax=60, tol=1e-12)
+    u_tight = np.zeros(shape)
+    st.solve_face(st.build_levels_face(op, 4), u_tight, f, cc.Params(tol=1e-13, kmax=60, coarsest=4))
+    ut = _t(np.zeros(shape))
+    assert fas.fas_solve(ctx_t, ut, _t(f)).converged
+    assert _rel(_n(ut), u_tight) <= 1e-10
 
 
 def test_face_grid_rejections(cuda_lib):
@@ -146,21 +152,22 @@ def test_face_grid_rejections(cuda_lib):
 # projection step
 # ---------------------------------------------------------------------------------------------
 
-def _fas_params(fas, precision, kmax, coarse_exact=0):
+def _fas_params(fas, precision, kmax, coarse_exact=0, tol=1e-10):
     p = fas.fas_default_params()
     p.precision = precision
     p.kmax = kmax
     p.coarse_exact = coarse_exact
     p.coarsest = 4
+    p.tol = tol
     return p
 
 
-def _ns_pair(fas, shape, precision, Re=100.0, dt=1e-3, lid=(1.0, 0.0, 0.0), order=1):
+def _ns_pair(fas, shape, precision, Re=100.0, dt=1e-3, lid=(1.0, 0.0, 0.0), order=1, tol=1e-10):
     h = 1.0 / shape[-1]
-    ns = fas.ns_create(shape, h, Re, dt, lid=lid, order=order, solver=_fas_params(fas, precision, 40),
-                       pressure=_fas_params(fas, precision, 60, 1))
-    prm = st.NSParams(Re=Re, dt=dt, lid=lid, solver=cc.Params(tol=1e-10, kmax=40, coarsest=4),
-                      pressure=cc.Params(tol=1e-10, kmax=60, coarsest=4, coarse_exact=True))
+    ns = fas.ns_create(shape, h, Re, dt, lid=lid, order=order, solver=_fas_params(fas, precision, 40, tol=tol),
+                       pressure=_fas_params(fas, precision, 60, 1, tol=tol))
+    prm = st.NSParams(Re=Re, dt=dt, lid=lid, solver=cc.Params(tol=tol, kmax=40, coarsest=4),
+                      pressure=cc.Params(tol=tol, kmax=60, coarsest=4, coarse_exact=True))
     return ns, prm, h
 
 
@@ -197,11 +204,13 @@ def test_projection_step_matches_oracle_fp64(cuda_lib, shape):
 
 @pytest.mark.parametrize("shape", [(64, 64), (32, 32, 32)])
 def test_projection_step_mixed_matches_oracle(cuda_lib, shape):
-    """Mixed-precision solves inside the step: every field within 1e-10 relative (2-norm) of the
-    oracle's float64 step, which is what two solutions converged to 1e-10 residual can agree to."""
+    """Mixed-precision solves inside the step: every field within 1e-10 relative max-norm of the
+    oracle's float64 step. Every solve on both sides is taken to 1e-12 relative residual, so that the
+    comparison measures the mixed-precision solver rather than where two iterations that both meet a
+    1e-10 residual happened to stop."""
     fas = cuda_lib
     dim = len(shape)
-    ns, prm, h = _ns_pair(fas, shape, 1, dt=2e-3)
+    ns, prm, h = _ns_pair(fas, shape, 1, dt=2e-3, tol=1e-12)
     ref = ns_state(shape, 541)
     gpu = {k: _t(v) for k, v in ref.items()}
     for step in range(2):
@@ -209,7 +218,7 @@ def test_projection_step_mixed_matches_oracle(cuda_lib, shape):
         st.projection_step(ref, shape, h, prm)
         assert all(infos[a].converged for a in range(dim)) and infos[3].converged
         for k in _fields_dim(dim):
-            assert _rel2(_n(gpu[k]), ref[k]) <= 1e-9, (step, k)
+            assert _rel(_n(gpu[k]), ref[k]) <= 1e-10, (step, k, _rel(_n(gpu[k]), ref[k]))
 
 
 def test_projection_step_2d_cavity_from_rest(cuda_lib):
@@ -389,9 +398,11 @@ def test_second_order_step_matches_oracle_fp64(cuda_lib, shape):
 
 @pytest.mark.parametrize("shape", [(64, 64), (16, 32, 32)])
 def test_second_order_step_mixed_matches_oracle(cuda_lib, shape):
+    """Second-order step with mixed-precision solves: every field within 1e-10 relative max-norm of
+    the oracle's float64 step, every solve on both sides taken to 1e-12 relative residual."""
     fas = cuda_lib
     dim = len(shape)
-    ns, prm, h = _ns_pair(fas, shape, 1, dt=2e-3, order=2)
+    ns, prm, h = _ns_pair(fas, shape, 1, dt=2e-3, order=2, tol=1e-12)
     ref = _state2(shape, 571)
     gpu = {k: _t(v) for k, v in ref.items()}
     for step in range(2):
@@ -399,7 +410,7 @@ def test_second_order_step_mixed_matches_oracle(cuda_lib, shape):
         st.projection_step2(ref, shape, h, prm)
         assert all(infos[a].converged for a in range(dim)) and infos[3].converged
         for k in _fields_dim(dim):
-            assert _rel2(_n(gpu[k]), ref[k]) <= 1e-9, (step, k)
+            assert _rel(_n(gpu[k]), ref[k]) <= 1e-10, (step, k, _rel(_n(gpu[k]), ref[k]))
 
 
 def test_order_rejected(cuda_lib):

@@ -2,7 +2,8 @@
 
 Bars: float64 single operators within a few ulps (1e-14 relative); float64 V-cycle iterates within
 1e-12 relative max-norm for cycles 1..8; converged float64 and mixed-precision solutions within 1e-10
-relative of the oracle's converged solution.
+relative max-norm of the oracle's converged solution (where two solves stopped at the 1e-10 residual
+could differ by more, the GPU side is solved tighter, never the bar widened).
 """
 import math
 
@@ -133,15 +134,17 @@ def test_symmetric_ordering_iterates(cuda_lib, shape, coarsest):
     um = _t(random_field(shape, 221))
     fas.fas_vcycle(ctx, um, fg)
     assert _rel(_n(um), _n(uf)) > 1e-8
-    # mixed precision reaches the oracle's converged solution
+    # mixed precision reaches the oracle's converged solution: both sides are solved past the 1e-10
+    # bar (GPU 1e-12, oracle 1e-13) so that the max-norm comparison measures the solver, not where two
+    # iterations that both satisfy a 1e-10 residual happened to stop
     _, ctx_m = _pair(fas, shape, h, 1.0, 2e-3, 1.0, _bc("mixed", dim), coarsest=coarsest,
-                     ordering=fas.FAS_ORDER_SYMMETRIC, precision=fas.FAS_MIXED)
+                     ordering=fas.FAS_ORDER_SYMMETRIC, precision=fas.FAS_MIXED, tol=1e-12, kmax=60)
     u_ref = np.zeros(shape)
     assert cc.solve(levels, u_ref, f, cc.Params(coarsest=coarsest, ordering="1234-4321", tol=1e-13,
                                                 kmax=60)).converged
     um = _t(np.zeros(shape))
     assert fas.fas_solve(ctx_m, um, fg).converged
-    assert _rel(_n(um), u_ref) < 1e-9
+    assert _rel(_n(um), u_ref) <= 1e-10
 
 
 def test_symmetric_ordering_argument_checks(cuda_lib):
@@ -173,7 +176,8 @@ def test_vcycle_iterates_variable_kappa(cuda_lib):
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("shape", [(256, 256), (1024, 1024), (64, 64, 64)])
 def test_converged_solution(cuda_lib, precision, shape):
-    """Solve to 1e-10 relative residual; compare with the oracle solved to 1e-13."""
+    """Solve to 1e-10 relative residual; compare with the oracle solved to 1e-13, within 1e-10
+    relative max-norm."""
     fas = cuda_lib
     h = 1.0 / shape[-1]
     op, ctx = _pair(fas, shape, h, 1.0, 1e-3, 1.0, (N_,) * (2 * len(shape)), coarsest=4, precision=precision)
@@ -204,18 +208,21 @@ def test_heat_run_small_matches_oracle(cuda_lib):
 
 
 def test_singular_poisson_coarse_exact(cuda_lib):
+    """Singular all-Neumann Poisson (alpha = 0, reading G7), float64: the GPU solve to 1e-13 relative
+    residual (the operator's conditioning, about (2/(pi h))^2, turns a residual of 1e-13 into a
+    solution error of about 1e-10) against the oracle's to 1e-14, within 1e-10 relative max-norm."""
     fas = cuda_lib
     shape = (64, 64)
-    op, ctx = _pair(fas, shape, 1.0 / 64, 0.0, 1.0, 1.0, (N_,) * 4, coarsest=4, coarse_exact=1, kmax=100,
-                    tol=1e-11)
+    op, ctx = _pair(fas, shape, 1.0 / 64, 0.0, 1.0, 1.0, (N_,) * 4, coarsest=4, coarse_exact=1, kmax=200,
+                    tol=1e-13)
     f = random_field(shape, 241, -1, 1)
     u_ref = np.zeros(shape)
-    cc.solve(cc.build_levels(op, 4), u_ref, f, cc.Params(tol=1e-13, kmax=200, coarsest=4, coarse_exact=True))
+    cc.solve(cc.build_levels(op, 4), u_ref, f, cc.Params(tol=1e-14, kmax=300, coarsest=4, coarse_exact=True))
     ug = _t(np.zeros(shape))
     info = fas.fas_solve(ctx, ug, _t(f))
     assert info.converged
     assert abs(float(_n(ug).mean())) < 1e-12
-    assert _rel(_n(ug), u_ref) < 1e-9
+    assert _rel(_n(ug), u_ref) <= 1e-10
 
 
 def test_error_statuses(cuda_lib):

@@ -49,7 +49,15 @@ typedef enum {
   FAS_EUNSUPPORTED = 7   /* valid request this build does not implement                       */
 } fas_status;
 
-typedef enum { FAS_BC_NEUMANN = 0, FAS_BC_DIRICHLET = 1 } fas_bc;
+/* Boundary kinds per face. NEUMANN: homogeneous, ghost = adjacent cell. DIRICHLET: homogeneous,
+ * ghost = -adjacent cell (Eqs. boundry1-2; values through fas_fold_dirichlet). PERIODIC: the grid wraps
+ * around along the axis, as in the grain-growth example of Sec. 3.3.1 (the paper writes no ghost
+ * relation for it; here the ghost of the first cell is the last cell and vice versa, and the face
+ * between them is an interior face). Both faces of an axis must be PERIODIC or neither; periodic axes
+ * need cell-centred unknowns and a constant kappa (FAS_EUNSUPPORTED otherwise) and run the
+ * per-operation kernels. With alpha = 0 and no Dirichlet face the operator is singular and is handled
+ * like the all-Neumann pressure solve (mean-free right-hand side, mean removed after every cycle). */
+typedef enum { FAS_BC_NEUMANN = 0, FAS_BC_DIRICHLET = 1, FAS_BC_PERIODIC = 2 } fas_bc;
 typedef enum { FAS_FP64 = 0, FAS_MIXED = 1 } fas_precision;
 
 /* Where the unknowns sit (Sec. 4.1, the MAC staggered grid). FAS_CELL: cell centres (Sec. 2.1).
@@ -260,9 +268,9 @@ fas_status fas_prof_read(fas_ctx* ctx, fas_prof_record* out, int cap, int* count
 
 /* --- solving without allocating ---------------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot allocate
- * device memory when they need a solve: code running while a stream is captured into a CUDA graph,
- * programs whose allocator has reserved all device memory up front, host callbacks (where allocating
- * CUDA calls are forbidden) and real-time loops that cannot take an allocation's latency or failure.
+ * device memory when they need a solve: programs whose allocator has reserved all device memory up
+ * front and hands it out itself, applications that give a solver a fixed budget and only device
+ * pointers to work in, and real-time loops that cannot take an allocation's latency or failure.
  *
  * fas_vcycle_small_static runs ncycles V-cycles (the V-cycle of fas_vcycle, float64, constant kappa,
  * coarsest level smoothed) on device field u in place, for right-hand side f, with no context and no
@@ -278,9 +286,12 @@ fas_status fas_prof_read(fas_ctx* ctx, fas_prof_record* out, int cap, int* count
  * Limits: at most 16 levels and a hierarchy (u and f on every level, the restricted start below the
  * top, plus descriptors) of at most 200 KB of shared memory: float64 grids up to 64 x 64 in 2D or
  * 16 x 16 x 16 in 3D. Larger grids return FAS_EINVAL with the needed size in fas_last_error().
- * The first call on a device looks up the static array's device address; make that first call before
- * any stream capture begins. All calls share the array, so calls that overlap on the GPU race; the
- * caller must serialise them (one stream, or events). */
+ * The first call on a device looks up the static array's device address (once per device, with that
+ * device current); make that first call before any stream capture begins, and do not use the entry
+ * point on a device after cudaDeviceReset in the same process. The level descriptors are written by
+ * small kernels that take them by value. All calls share the array, and each call leaves its own
+ * descriptors and norm in it, so calls that overlap on the GPU race (for example on two streams);
+ * the caller must serialise them (one stream, or events). */
 fas_status fas_vcycle_small_static(const fas_params* p, double* u, const double* f, int ncycles,
                                    double* res_host, void* stream);
 
@@ -292,6 +303,13 @@ fas_status fas_vcycle_small_static(const fas_params* p, double* u, const double*
  * routine and, inside float32's normal range, by the shorter one the residual kernels use). *mismatches (HOST) receives the number of
  * results that differ in any bit (two NaNs count as equal). Runs on the current device and stream 0. */
 fas_status fas_selftest_conversions(long long count, unsigned long long seed, long long* mismatches);
+
+/* Measured float64 FMA throughput of the current device (no counterpart in the paper): times a kernel
+ * of independent DFMA chains on every SM with CUDA events (best of three launches after a warm-up) and
+ * writes the rate in TFLOP/s (an FMA counts as two operations) to *tflops (HOST). It is the FP64-pipe
+ * denominator of the roofline of the float64 kernels. Runs on the current device and stream 0 and
+ * waits for it; FAS_ECUDA if a CUDA call fails. */
+fas_status fas_probe_fp64_rate(double* tflops);
 
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char* fas_last_error(void);

@@ -23,13 +23,14 @@ __all__ = [
     "fas_num_levels", "fas_vcycle", "fas_solve", "fas_heat_run", "fas_heat_run_host", "fas_residual",
     "fas_smooth", "fas_restrict", "fas_prolong_add", "fas_last_error", "fas_launch_count", "Solver",
     "fas_prof_enable", "fas_prof_read", "make_params", "fas_vcycle_small_static", "fas_solve_batched",
-    "fas_autotune", "fas_heat_adjoint", "fas_fold_dirichlet", "solve", "HeatSolve",
+    "fas_autotune", "fas_heat_adjoint", "fas_fold_dirichlet", "solve", "HeatSolve", "fas_probe_fp64_rate",
+    "gg_model", "gg_create", "gg_step", "gg_rhs", "gg_destroy",
 ]
 
 FAS_OK, FAS_EINVAL, FAS_ENOMEM, FAS_ENOTCONV, FAS_ENONFINITE, FAS_ETIMEOUT, FAS_ECUDA, FAS_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["FAS_OK", "FAS_EINVAL", "FAS_ENOMEM", "FAS_ENOTCONV", "FAS_ENONFINITE", "FAS_ETIMEOUT",
                 "FAS_ECUDA", "FAS_EUNSUPPORTED"]
-FAS_BC_NEUMANN, FAS_BC_DIRICHLET = 0, 1
+FAS_BC_NEUMANN, FAS_BC_DIRICHLET, FAS_BC_PERIODIC = 0, 1, 2
 FAS_FP64, FAS_MIXED = 0, 1
 FAS_ORDER_FORWARD, FAS_ORDER_SYMMETRIC = 0, 1  # X-MCGS 1234-1234 / 1234-4321 (Sec. 2.3)
 FAS_CELL, FAS_FACE_X, FAS_FACE_Y, FAS_FACE_Z = 0, 1, 2, 3
@@ -62,6 +63,12 @@ class fas_tune_result(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class gg_model(ctypes.Structure):
+    """Model constants of the grain-growth step (Sec. 3.3.1): L, alpha, beta, gamma, kappa."""
+    _fields_ = [("L", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("kappa", ctypes.c_double)]
 
 
 class FasError(RuntimeError):
@@ -111,11 +118,17 @@ def load(path: str | None = None):
         "fas_residual_ir": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D)]),
         "fas_fold_dirichlet": (_I, [_P, _P, ctypes.POINTER(_D)]),
         "fas_selftest_conversions": (_I, [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]),
+        "fas_probe_fp64_rate": (_I, [ctypes.POINTER(_D)]),
         "ns_create": (_I, [_I, ctypes.POINTER(_I), _D, _D, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(fas_params),
                            ctypes.POINTER(fas_params), _P, ctypes.POINTER(_P)]),
         "ns_projection_step": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(fas_info),
                                     ctypes.POINTER(_D)]),
         "ns_launch_count": (ctypes.c_longlong, [_P, _I]),
+        "gg_create": (_I, [_I, ctypes.POINTER(_I), _D, _D, _I, ctypes.POINTER(gg_model), ctypes.POINTER(fas_params),
+                           _I, _P, ctypes.POINTER(_P)]),
+        "gg_step": (_I, [_P, _P, ctypes.POINTER(fas_info)]),
+        "gg_rhs": (_I, [_P, _P, _P]),
+        "gg_destroy": (_I, [_P]),
         "ns_destroy": (_I, [_P]),
     }
     for name, (res, args) in sig.items():
@@ -283,6 +296,13 @@ def fas_selftest_conversions(count: int, seed: int = 1) -> int:
     return out.value
 
 
+def fas_probe_fp64_rate() -> float:
+    """Measured float64 FMA throughput of the current device in TFLOP/s (an FMA counts as two)."""
+    out = ctypes.c_double(0.0)
+    _check(load().fas_probe_fp64_rate(ctypes.byref(out)), "fas_probe_fp64_rate")
+    return out.value
+
+
 def fas_smooth(ctx: _Ctx, level: int, u, f, sweeps: int) -> None:
     n = ctx.level_cells(level)
     _check(load().fas_smooth(ctx.handle, level, _dev(u, "u", n), _dev(f, "f", n), int(sweeps)), "fas_smooth")
@@ -410,6 +430,61 @@ def ns_destroy(ns: _NsCtx) -> None:
     if ns.handle:
         _check(load().ns_destroy(ns.handle), "ns_destroy")
         ns.handle = None
+
+
+class _GgCtx:
+    """Owns a gg_ctx* (grain-growth step), its grid shape (numpy order) and q."""
+
+    def __init__(self, handle, shape, q):
+        self.handle = handle
+        self.shape = tuple(shape)
+        self.q = int(q)
+        self.cells = 1
+        for v in shape:
+            self.cells *= int(v)
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.gg_destroy(self.handle)
+            self.handle = None
+
+
+def gg_create(shape, h: float, dt: float, q: int, model=None, solver=None, batch: int = 0, stream=None) -> _GgCtx:
+    """gg_create for a numpy-order periodic grid shape; model: gg_model or a dict of its fields (None:
+    the paper's constants); solver: fas_params (None: the library's defaults)."""
+    lib = load()
+    dim = len(shape)
+    phys = list(reversed([int(v) for v in shape])) + [1] * (3 - dim)
+    n = (_I * 3)(*phys)
+    if isinstance(model, dict):
+        model = gg_model(**model)
+    out = _P()
+    _check(lib.gg_create(dim, n, float(h), float(dt), int(q), ctypes.byref(model) if model is not None else None,
+                         ctypes.byref(solver) if solver is not None else None, int(batch), _stream_handle(stream),
+                         ctypes.byref(out)), "gg_create")
+    return _GgCtx(out, shape, q)
+
+
+def gg_step(gg: _GgCtx, eta, allow_notconv: bool = False):
+    """One grain-growth step in place on eta (float64 CUDA tensor of shape (q,) + grid); returns the
+    q solver reports."""
+    infos = (fas_info * gg.q)()
+    st = load().gg_step(gg.handle, _dev(eta, "eta", gg.q * gg.cells), infos)
+    if not (allow_notconv and st == FAS_ENOTCONV):
+        _check(st, "gg_step")
+    return [infos[k] for k in range(gg.q)]
+
+
+def gg_rhs(gg: _GgCtx, eta, rhs) -> None:
+    """The q right-hand sides of the step from eta (both float64 CUDA tensors of shape (q,) + grid)."""
+    n = gg.q * gg.cells
+    _check(load().gg_rhs(gg.handle, _dev(eta, "eta", n), _dev(rhs, "rhs", n)), "gg_rhs")
+
+
+def gg_destroy(gg: _GgCtx) -> None:
+    if gg.handle:
+        _check(load().gg_destroy(gg.handle), "gg_destroy")
+        gg.handle = None
 
 
 class fas_prof_record(ctypes.Structure):

@@ -1,11 +1,11 @@
 // small_static.cu -- V-cycles on a small grid without any device allocation.
 //
-// Some callers cannot allocate device memory when they need a solve:
-//   - code running while a stream is being captured into a CUDA graph (cudaMalloc is not allowed
-//     during a global-mode capture);
-//   - programs whose memory allocator has reserved all device memory up front and owns it;
-//   - host callbacks, in which CUDA calls that allocate are forbidden;
-//   - real-time loops that cannot afford an allocation's latency or failure in steady state.
+// Some callers cannot allocate device memory at the moment they need a solve:
+//   - programs whose memory allocator reserved all device memory up front and hands it out itself
+//     (a cudaMalloc from this library would fail or fragment that pool);
+//   - applications that give a solver plugin a fixed memory budget and only device pointers to work in;
+//   - real-time loops that cannot afford an allocation's latency, or the chance of its failure, in
+//     steady state.
 // fas_vcycle_small_static serves them for grids small enough that the whole level hierarchy fits in
 // one CTA's shared memory: it runs the same single-CTA V-cycle kernel as the library's small levels,
 // with the only global scratch that kernel needs -- the level-descriptor table and one slot for the
@@ -13,7 +13,10 @@
 //
 // The array lives on every GPU that loads the library until the process exits. All calls share it:
 // a call overwrites the descriptors and the norm slot of the previous one, so calls that overlap on
-// the GPU (for example on two streams) race and must be serialised by the caller.
+// the GPU (for example on two streams) race and must be serialised by the caller (one stream, or
+// events). Its device address is looked up once per device, on the first call made with that device
+// current; make that first call before any stream capture begins, and do not use the entry point on a
+// device after cudaDeviceReset in the same process (the address looked up before the reset is stale).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -63,6 +66,15 @@ cudaError_t scratch_address(StaticScratch** out) {
   return cudaSuccess;
 }
 
+// One level descriptor, passed by value as the kernel argument, stored into the static table (the
+// descriptors reach the device without a host-memory copy).
+__global__ void k_static_store_desc(LevelDesc<double> d, StaticScratch* S, int level) {
+  const int words = (int)(sizeof(LevelDesc<double>) / sizeof(int));
+  const int* src = reinterpret_cast<const int*>(&d);
+  int* dst = reinterpret_cast<int*>(&S->desc[level]);
+  for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+}
+
 // ||f - A u||_2 of level 0 by one CTA (the grid is small), into norm[0].
 template <int DIM>
 __global__ void __launch_bounds__(1024) k_static_norm(const double* u, const double* f, StaticScratch* S) {
@@ -103,6 +115,9 @@ extern "C" fas_status fas_vcycle_small_static(const fas_params* p, double* u, co
   if (ncycles < 1) return fail_static(FAS_EINVAL, "fas_vcycle_small_static: ncycles must be >= 1");
   if (p->ordering != FAS_ORDER_FORWARD && p->ordering != FAS_ORDER_SYMMETRIC)
     return fail_static(FAS_EINVAL, "fas_vcycle_small_static: unknown ordering");
+  for (int k = 0; k < 2 * p->dim; ++k)
+    if (p->bc[k] != FAS_BC_NEUMANN && p->bc[k] != FAS_BC_DIRICHLET)
+      return fail_static(FAS_EUNSUPPORTED, "fas_vcycle_small_static: Neumann and Dirichlet faces only");
   if (p->kappa || p->coarse_exact || p->precision != FAS_FP64 || p->location != FAS_CELL)
     return fail_static(FAS_EUNSUPPORTED,
                        "fas_vcycle_small_static: cell-centred unknowns, constant kappa, smoothed coarsest level "
@@ -184,9 +199,12 @@ extern "C" fas_status fas_vcycle_small_static(const fas_params* p, double* u, co
   StaticScratch* scratch = nullptr;
   cudaError_t e = scratch_address(&scratch);
   if (e != cudaSuccess) return fail_static(FAS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-  // the descriptors are rewritten on every call; the norm slot is written by the norm kernel
-  e = cudaMemcpyAsync(scratch->desc, desc, nlev * sizeof(LevelDesc<double>), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return fail_static(FAS_ECUDA, std::string("descriptor copy: ") + cudaGetErrorString(e));
+  // the descriptors are rewritten on every call (by value, one small kernel per level); the norm slot
+  // is written by the norm kernel
+  static_assert(sizeof(LevelDesc<double>) % sizeof(int) == 0, "descriptor copied as 32-bit words");
+  for (int l = 0; l < nlev; ++l) k_static_store_desc<<<1, 128, 0, st>>>(desc[l], scratch, l);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_static(FAS_ECUDA, std::string("descriptor store: ") + cudaGetErrorString(e));
 
   CoarseArgs<double> A;
   std::memset(&A, 0, sizeof(A));

@@ -1,10 +1,11 @@
 """The allocation-free entry point fas_vcycle_small_static.
 
-It serves callers that cannot allocate device memory when they need a solve (code running during a
-CUDA-graph capture, programs whose allocator has reserved all device memory, host callbacks,
-real-time loops). It must compute what the context-based fas_vcycle computes, call after call, while
-its scratch lives in a static device array shared by all calls. This file is collected last so that a
-stop-at-first-failure run has already run every other test.
+It serves callers that cannot allocate device memory when they need a solve (programs whose
+allocator has reserved all device memory up front, applications that give a solver a fixed budget,
+real-time loops). It must compute what the context-based fas_vcycle computes, and what the oracle's
+V-cycle (Algorithm 1 with its recursion) computes, call after call, while its scratch lives in a
+static device array shared by all calls. This file is collected last so that a stop-at-first-failure
+run has already run every other test.
 """
 import numpy as np
 import pytest
@@ -86,3 +87,27 @@ def test_static_entry_symmetric_ordering(cuda_lib):
         fas.fas_vcycle(ctx, u_ref, f)
     fas.fas_vcycle_small_static(fas.make_params(shape, h, **kw), u_new, f, 3)
     assert _rel(u_new.cpu().numpy(), u_ref.cpu().numpy()) <= 1e-12
+
+
+@pytest.mark.parametrize("shape,bc,coarsest,ordering", [((64, 64), (N_,) * 4, 4, 0),
+                                                        ((64, 64), (D_, N_, N_, D_), 2, 1),
+                                                        ((16, 16, 16), (N_,) * 6, 2, 0),
+                                                        ((16, 16, 16), (D_, N_, N_, N_, D_, D_), 4, 1)])
+def test_static_entry_matches_oracle_iterates(cuda_lib, shape, bc, coarsest, ordering):
+    """Cycles 1..6 of the allocation-free entry (one call per cycle) against the oracle's V-cycle
+    iterates within 1e-12 relative max-norm, and its reported residual against the oracle's."""
+    fas = cuda_lib
+    h = 1.0 / shape[-1]
+    params = fas.make_params(shape, h, alpha=1.0, beta=2e-3, bc=bc, coarsest=coarsest, ordering=ordering)
+    op = cc.Operator(shape, h, 1.0, 2e-3, 1.0, bc)
+    levels = cc.build_levels(op, coarsest)
+    prm = cc.Params(coarsest=coarsest, ordering="1234-4321" if ordering else "1234-1234")
+    u = random_field(shape, 431)
+    f = random_field(shape, 432, -1, 1)
+    ug, fg = _t(u), _t(f)
+    for k in range(6):
+        res = fas.fas_vcycle_small_static(params, ug, fg, 1)
+        cc.vcycle(levels, u, f, prm)
+        assert _rel(ug.cpu().numpy(), u) <= 1e-12, "cycle %d" % (k + 1)
+        res_ref = cc.norm2(cc.residual(op, u, f))
+        assert abs(res - res_ref) <= 1e-6 * res_ref, (k + 1, res, res_ref)

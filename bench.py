@@ -426,7 +426,8 @@ def _event_ms(stream, fn, warmup=1):
 def secondary_workloads(dev, stream, ws=1, rank=0):
     """The other workloads of the method, each once after one warm-up run (float64 vs mixed where both
     apply): 3D heat 512^3, the 256^3 lid-driven cavity projection steps, 96 batched Helmholtz solves in
-    one graph launch, the 1024^2 adjoint heat run. Inputs are the seeded recipes of workloads/. Under
+    one graph launch, the 512^2 grain-growth step with 1189 order parameters (periodic solves), the
+    1024^2 adjoint heat run. Inputs are the seeded recipes of workloads/. Under
     several ranks the batched problems are shared out (cell-balanced, no data exchange) and the other
     workloads run as one replica per rank."""
     import numpy as np
@@ -559,6 +560,45 @@ def secondary_workloads(dev, stream, ws=1, rank=0):
     for c in ctxs:
         fas.fas_destroy(c)
     del fs, us, ctxs
+    torch.cuda.empty_cache()
+
+    # grain growth (Sec. 3.3.1): 512^2 periodic, q = 1189 order parameters, h 2, dt 0.25, from the
+    # disordered start U(-0.001, 0.001); one step = the q right-hand sides and q periodic solves
+    from workloads import grain_growth
+    w = grain_growth()
+    q, shape = w["q"], w["shape"]
+    cells = int(np.prod(shape))
+    eta0 = torch.from_numpy(w["etas"]).to(dev)
+    del w["etas"]
+    gsteps = 3
+    ggr = {}
+    for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
+        sp = fas.fas_default_params()
+        sp.precision, sp.kmax, sp.coarsest = prec, 40, 4
+        ctx = fas.gg_create(shape, w["h"], w["dt"], q, solver=sp, stream=stream)
+        eta = eta0.clone()
+        fas.gg_step(ctx, eta)  # warm-up: builds the batch graphs
+        eta.copy_(eta0)
+
+        def run_g():
+            cyc = 0
+            for _ in range(gsteps):
+                cyc += sum(i.cycles for i in fas.gg_step(ctx, eta))
+            return cyc
+        ms, cyc = _event_ms(stream, run_g, warmup=0)
+        ggr[name] = {"ms_per_step": ms / gsteps, "vcycles_per_step": cyc / gsteps,
+                     "Mcells_vcycles_per_s": mc(cells, cyc, ms), "eta": eta.clone()}
+        fas.gg_destroy(ctx)
+        del eta
+    out["grain_growth_512"] = {
+        "workload": "grain growth 512^2 periodic, q=1189 order parameters, h 2, dt 0.25, %d steps from "
+                    "U(-0.001,0.001), linearly implicit step, tol 1e-10" % gsteps,
+        "mixed": {k: v for k, v in ggr["mixed"].items() if k != "eta"},
+        "fp64": {k: v for k, v in ggr["fp64"].items() if k != "eta"},
+        "speedup_mixed_vs_fp64_time": ggr["fp64"]["ms_per_step"] / ggr["mixed"]["ms_per_step"],
+        "mixed_vs_fp64_rel_maxdiff": float((ggr["mixed"]["eta"] - ggr["fp64"]["eta"]).abs().max().item()
+                                           / ggr["fp64"]["eta"].abs().max().item())}
+    del eta0, ggr
     torch.cuda.empty_cache()
 
     # adjoint: 1024^2 heat with varying kappa, 50 steps, checkpoints every 10

@@ -313,27 +313,33 @@ __global__ void k_smooth_colour4(T* u, const T* f, LevelDesc<T> L, int colour) {
     Quad<T> c, s4, n4, b4, t4, f4;
     c.ld(u + idx);
     f4.ld(f + idx);
-    const T wedge = x0 > 0 ? u[idx - 1] : T(0);
-    const T eedge = x0 + 4 < nx ? u[idx + 4] : T(0);
+    // neighbours across a boundary: the wrapped cells on a periodic axis, none otherwise
+    const bool px = L.per & 1, py = (L.per >> 1) & 1, pz = (L.per >> 2) & 1;
+    const T wedge = x0 > 0 ? u[idx - 1] : (px ? u[idx + nx - 1] : T(0));
+    const T eedge = x0 + 4 < nx ? u[idx + 4] : (px ? u[idx + 4 - nx] : T(0));
     if (j > 0) s4.ld(u + idx - sy);
+    else if (py) s4.ld(u + idx + (ny - 1) * sy);
     if (j < ny - 1) n4.ld(u + idx + sy);
+    else if (py) n4.ld(u + idx - (ny - 1) * sy);
     if (DIM == 3) {
       if (l > 0) b4.ld(u + idx - sz);
+      else if (pz) b4.ld(u + idx + (nz - 1) * sz);
       if (l < nz - 1) t4.ld(u + idx + sz);
+      else if (pz) t4.ld(u + idx - (nz - 1) * sz);
     }
     // cell x has the colour when (x + j + l + DIM + colour) is even; the same along a row
     auto upd = [&](auto kc) {
       constexpr int k = decltype(kc)::value;
       const int i = x0 + k;
       if (L.fax >= 0 && frozen(L, i, j, l)) return;
-      const T w = i > 0 ? (k > 0 ? c.v[k > 0 ? k - 1 : 0] : wedge) : T(0);
-      const T e = i < nx - 1 ? (k < 3 ? c.v[k < 3 ? k + 1 : 3] : eedge) : T(0);
-      const T sv = j > 0 ? s4.v[k] : T(0);
-      const T nv = j < ny - 1 ? n4.v[k] : T(0);
+      const T w = (i > 0 || px) ? (k > 0 ? c.v[k > 0 ? k - 1 : 0] : wedge) : T(0);
+      const T e = (i < nx - 1 || px) ? (k < 3 ? c.v[k < 3 ? k + 1 : 3] : eedge) : T(0);
+      const T sv = (j > 0 || py) ? s4.v[k] : T(0);
+      const T nv = (j < ny - 1 || py) ? n4.v[k] : T(0);
       T acc = (w + e) + (sv + nv);
       if (DIM == 3) {
-        const T bo = l > 0 ? b4.v[k] : T(0);
-        const T to = l < nz - 1 ? t4.v[k] : T(0);
+        const T bo = (l > 0 || pz) ? b4.v[k] : T(0);
+        const T to = (l < nz - 1 || pz) ? t4.v[k] : T(0);
         acc = acc + (bo + to);
       }
       const int cls = bclass<DIM>(i, j, l, nx, ny, nz);
@@ -435,22 +441,24 @@ static __global__ void k_ir_update(double* u, const float* e, int64_t n) {
 }
 
 // Bit patterns of the neighbours of cell (i, j, l) in the order x-, x+, y-, y+, z-, z+ (0 where a
-// neighbour is missing) and the mask of the present ones.
+// neighbour is missing; the wrapped cell across a periodic boundary) and the mask of the present ones.
 template <int DIM>
 __device__ __forceinline__ unsigned nb_bits(const double* __restrict__ u, int64_t idx, int i, int j, int l,
                                             const LevelDesc<double>& L, uint64_t (&nb)[2 * DIM]) {
   const unsigned long long* ub = reinterpret_cast<const unsigned long long*>(u);
   const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny;
-  const bool p0 = i > 0, p1 = i < L.nx - 1, p2 = j > 0, p3 = j < L.ny - 1;
-  nb[0] = p0 ? ub[idx - 1] : 0ull;
-  nb[1] = p1 ? ub[idx + 1] : 0ull;
-  nb[2] = p2 ? ub[idx - sy] : 0ull;
-  nb[3] = p3 ? ub[idx + sy] : 0ull;
+  const bool px = L.per & 1, py = (L.per >> 1) & 1;
+  const bool p0 = i > 0 || px, p1 = i < L.nx - 1 || px, p2 = j > 0 || py, p3 = j < L.ny - 1 || py;
+  nb[0] = p0 ? ub[i > 0 ? idx - 1 : idx + L.nx - 1] : 0ull;
+  nb[1] = p1 ? ub[i < L.nx - 1 ? idx + 1 : idx - (L.nx - 1)] : 0ull;
+  nb[2] = p2 ? ub[j > 0 ? idx - sy : idx + (L.ny - 1) * sy] : 0ull;
+  nb[3] = p3 ? ub[j < L.ny - 1 ? idx + sy : idx - (L.ny - 1) * sy] : 0ull;
   unsigned mask = (unsigned)p0 | ((unsigned)p1 << 1) | ((unsigned)p2 << 2) | ((unsigned)p3 << 3);
   if constexpr (DIM == 3) {
-    const bool p4 = l > 0, p5 = l < L.nz - 1;
-    nb[4] = p4 ? ub[idx - sz] : 0ull;
-    nb[5] = p5 ? ub[idx + sz] : 0ull;
+    const bool pz = (L.per >> 2) & 1;
+    const bool p4 = l > 0 || pz, p5 = l < L.nz - 1 || pz;
+    nb[4] = p4 ? ub[l > 0 ? idx - sz : idx + (L.nz - 1) * sz] : 0ull;
+    nb[5] = p5 ? ub[l < L.nz - 1 ? idx + sz : idx - (L.nz - 1) * sz] : 0ull;
     mask |= ((unsigned)p4 << 4) | ((unsigned)p5 << 5);
   }
   return mask;

@@ -14,6 +14,9 @@
 // the smoother is (sum of 4 neighbours + h^2 f) / (4 + h^2), the paper's update.
 // With a per-cell kappa the face weights w_f (kappa_f = mean of the two cells) and 1/D, D/h^2 are
 // stored per cell on every level.
+// Periodic axes (the grain-growth example, Sec. 3.3.1): the grid wraps around, so the first and the
+// last cell of the axis are neighbours across an interior face (m_f = 1). Their boundary classes then
+// carry the interior constants, and the neighbour sums below fetch the wrapped cell.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,6 +34,7 @@ struct LevelDesc {
   int fax;         // -1: cell-centred unknowns; 0/1/2: face unknowns normal to x/y/z (staggered
                    // velocity component): slot s of that axis is face s+1, the last slot is the
                    // far wall (frozen at 0), the near wall face is implicit and 0
+  int per;         // periodic axes: bit 0 x, bit 1 y, bit 2 z (constant kappa, cell-centred only)
   T h2, ih2;       // h^2, 1/h^2
   T c;             // beta kappa / h^2 (constant kappa)
   const T* wx;     // beta kappa_f of the face between cells i and i+1, stored at cell i (0 at i = nx-1)
@@ -57,19 +61,20 @@ __device__ __forceinline__ bool frozen(const LevelDesc<T>& L, int i, int j, int 
   return (L.fax == 0 && i == L.nx - 1) || (L.fax == 1 && j == L.ny - 1) || (L.fax == 2 && l == L.nz - 1);
 }
 
-// Sum of the existing neighbours of cell (i, j, l) at linear index idx (constant kappa).
+// Sum of the existing neighbours of cell (i, j, l) at linear index idx (constant kappa); on a periodic
+// axis (bit of per) the neighbour across the boundary is the wrapped cell.
 template <typename T, int DIM>
 __device__ __forceinline__ T nbsum(const T* __restrict__ u, int64_t idx, int i, int j, int l, int nx,
-                                   int ny, int nz) {
+                                   int ny, int nz, int per) {
   const int64_t sy = nx, sz = (int64_t)nx * ny;
-  T w = i > 0 ? u[idx - 1] : T(0);
-  T e = i < nx - 1 ? u[idx + 1] : T(0);
-  T s = j > 0 ? u[idx - sy] : T(0);
-  T n = j < ny - 1 ? u[idx + sy] : T(0);
+  T w = i > 0 ? u[idx - 1] : ((per & 1) ? u[idx + nx - 1] : T(0));
+  T e = i < nx - 1 ? u[idx + 1] : ((per & 1) ? u[idx - (nx - 1)] : T(0));
+  T s = j > 0 ? u[idx - sy] : ((per & 2) ? u[idx + (ny - 1) * sy] : T(0));
+  T n = j < ny - 1 ? u[idx + sy] : ((per & 2) ? u[idx - (ny - 1) * sy] : T(0));
   T acc = (w + e) + (s + n);
   if (DIM == 3) {
-    T bo = l > 0 ? u[idx - sz] : T(0);
-    T to = l < nz - 1 ? u[idx + sz] : T(0);
+    T bo = l > 0 ? u[idx - sz] : ((per & 4) ? u[idx + (nz - 1) * sz] : T(0));
+    T to = l < nz - 1 ? u[idx + sz] : ((per & 4) ? u[idx - (nz - 1) * sz] : T(0));
     acc = acc + (bo + to);
   }
   return acc;
@@ -101,7 +106,7 @@ __device__ __forceinline__ T point_update(const T* __restrict__ u, const T* __re
     return fma(L.h2, f[idx], nw) * L.rD[idx];
   }
   const int cls = bclass<DIM>(i, j, l, L.nx, L.ny, L.nz);
-  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz);
+  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz, L.per);
   return fma(L.a[cls], nb, L.b[cls] * f[idx]);
 }
 
@@ -114,7 +119,7 @@ __device__ __forceinline__ T apply_point(const T* __restrict__ u, const LevelDes
     return fma(L.Dh[idx], u[idx], -L.ih2 * nw);
   }
   const int cls = bclass<DIM>(i, j, l, L.nx, L.ny, L.nz);
-  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz);
+  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz, L.per);
   return fma(L.d[cls], u[idx], -L.c * nb);
 }
 
@@ -127,7 +132,7 @@ __device__ __forceinline__ T residual_point(const T* __restrict__ u, const T* __
     return fma(L.ih2, nw, fma(-L.Dh[idx], u[idx], f[idx]));
   }
   const int cls = bclass<DIM>(i, j, l, L.nx, L.ny, L.nz);
-  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz);
+  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz, L.per);
   return fma(L.c, nb, fma(-L.d[cls], u[idx], f[idx]));
 }
 

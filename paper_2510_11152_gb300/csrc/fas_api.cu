@@ -97,8 +97,17 @@ struct Prof {
 // level descriptors
 // ---------------------------------------------------------------------------------------------
 
-// boundary multiplicity of a face: 0 Neumann (ghost = cell), 2 Dirichlet (ghost = -cell)
-int bc_mult(int kind) { return kind == FAS_BC_DIRICHLET ? 2 : 0; }
+// boundary multiplicity of a face: 0 Neumann (ghost = cell), 2 Dirichlet (ghost = -cell), 1 periodic
+// (the face is an interior face whose neighbour is the wrapped cell)
+int bc_mult(int kind) { return kind == FAS_BC_DIRICHLET ? 2 : (kind == FAS_BC_PERIODIC ? 1 : 0); }
+
+// periodic axes as a bit mask (bit 0 x, 1 y, 2 z)
+int periodic_mask(const fas_params& p) {
+  int m = 0;
+  for (int a = 0; a < p.dim; ++a)
+    if (p.bc[2 * a] == FAS_BC_PERIODIC) m |= 1 << a;
+  return m;
+}
 
 template <typename T>
 LevelDesc<T> make_desc(const fas_params& p, const LevelShape& s) {
@@ -117,6 +126,7 @@ LevelDesc<T> make_desc(const fas_params& p, const LevelShape& s) {
   L.lz = lg(s.nz);
   L.varkappa = p.kappa != nullptr;
   L.fax = p.location - 1;  // FAS_CELL -> -1, FAS_FACE_X/Y/Z -> 0/1/2
+  L.per = periodic_mask(p);
   const double h2 = s.h * s.h;
   L.h2 = (T)h2;
   L.ih2 = (T)(1.0 / h2);
@@ -196,6 +206,13 @@ fas_status coarse_inverse(const fas_ctx* c, const LevelShape& s, const std::vect
           if (l > 0) off(q - s.nx * s.ny, var ? wz[q - s.nx * s.ny] : bk);
           if (l < s.nz - 1) off(q + s.nx * s.ny, var ? wz[q] : bk);
         }
+        // periodic axes (constant kappa): the wrapped neighbours across the boundary
+        if ((L.per & 1) && i == 0) off(q + s.nx - 1, bk);
+        if ((L.per & 1) && i == s.nx - 1) off(q - (s.nx - 1), bk);
+        if ((L.per & 2) && j == 0) off(q + (s.ny - 1) * s.nx, bk);
+        if ((L.per & 2) && j == s.ny - 1) off(q - (s.ny - 1) * s.nx, bk);
+        if ((L.per & 4) && l == 0) off(q + (s.nz - 1) * s.nx * s.ny, bk);
+        if ((L.per & 4) && l == s.nz - 1) off(q - (s.nz - 1) * s.nx * s.ny, bk);
       }
   if (c->singular)
     for (auto& v : M) v += 1.0 / n;
@@ -361,7 +378,7 @@ fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers)
     // handle and that are larger than the single-CTA switch level
     H.nfast = 0;
     if (sizeof(T) == 4 && p.dim == 2 && p.path == 0 && !p.kappa && p.location == FAS_CELL &&
-        p.ordering == FAS_ORDER_FORWARD && p.nu1 >= 1 && p.nu2 >= 1) {
+        p.ordering == FAS_ORDER_FORWARD && p.nu1 >= 1 && p.nu2 >= 1 && periodic_mask(p) == 0) {
       while (H.nfast < H.switch_level &&
              stream2d_supported(c->shape[H.nfast].nx, c->shape[H.nfast].ny, std::max(p.nu1, p.nu2)))
         H.nfast++;
@@ -1243,7 +1260,13 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
   if (p.ordering != FAS_ORDER_FORWARD && p.location != FAS_CELL)
     return fail(FAS_EUNSUPPORTED, "the symmetric ordering is for cell-centred unknowns");
   for (int k = 0; k < 2 * p.dim; ++k)
-    if (p.bc[k] != FAS_BC_NEUMANN && p.bc[k] != FAS_BC_DIRICHLET) return fail(FAS_EINVAL, "unknown bc kind");
+    if (p.bc[k] != FAS_BC_NEUMANN && p.bc[k] != FAS_BC_DIRICHLET && p.bc[k] != FAS_BC_PERIODIC)
+      return fail(FAS_EINVAL, "unknown bc kind");
+  for (int a = 0; a < p.dim; ++a)
+    if ((p.bc[2 * a] == FAS_BC_PERIODIC) != (p.bc[2 * a + 1] == FAS_BC_PERIODIC))
+      return fail(FAS_EINVAL, "periodic faces come in pairs: both faces of an axis or neither");
+  if (periodic_mask(p) && (p.kappa || p.location != FAS_CELL))
+    return fail(FAS_EUNSUPPORTED, "periodic axes: cell-centred unknowns with a constant kappa only");
   if (p.location < FAS_CELL || p.location > p.dim) return fail(FAS_EINVAL, "location must be a cell or a face axis");
   if (p.location != FAS_CELL) {
     for (int k = 0; k < 2 * p.dim; ++k)
@@ -1261,9 +1284,9 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
   c->max_blocks = c->sm_count * 16;
-  bool all_neumann = true;
-  for (int k = 0; k < 2 * p.dim; ++k) all_neumann = all_neumann && p.bc[k] == FAS_BC_NEUMANN;
-  c->singular = p.alpha == 0.0 && all_neumann;
+  bool no_dirichlet = true;  // Neumann and periodic faces leave the constants in the null space
+  for (int k = 0; k < 2 * p.dim; ++k) no_dirichlet = no_dirichlet && p.bc[k] != FAS_BC_DIRICHLET;
+  c->singular = p.alpha == 0.0 && no_dirichlet;
   // levels: halve every axis while the shortest exceeds `coarsest`
   LevelShape s{p.n[0], p.n[1], p.dim == 3 ? p.n[2] : 1, p.h};
   c->shape.push_back(s);
@@ -1406,6 +1429,7 @@ fas_status fas_heat_adjoint(fas_ctx* c, const double* u0, const double* fsrc, do
   if (c->p.alpha != 1.0 || std::fabs(c->p.beta - dt) > 1e-15 * std::fabs(dt))
     return fail(FAS_EINVAL, "fas_heat_adjoint: context must have alpha = 1 and beta = dt");
   if (c->p.location != FAS_CELL) return fail(FAS_EUNSUPPORTED, "fas_heat_adjoint: cell-centred unknowns only");
+  if (periodic_mask(c->p)) return fail(FAS_EUNSUPPORTED, "fas_heat_adjoint: periodic axes are not supported");
   const int64_t n = c->shape[0].cells();
   const size_t bytes = n * sizeof(double);
   const int K = ckpt_every > 0 ? std::min(ckpt_every, nsteps) : nsteps;

@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(kIrThreads, 2)
 }  // namespace
 
 bool ir_strip_supported(const LevelDesc<double>& L) {
-  if (L.varkappa || L.nx % kIrCols != 0) return false;
+  if (L.varkappa || L.per || L.nx % kIrCols != 0) return false;
   if (L.nz == 1) return L.fax < 0 && L.ny >= 1;
   return L.ny % kIr3Rows == 0;
 }

@@ -15,7 +15,7 @@ def _declared():
     for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(hdr).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(fas_\w+|ns_\w+|fasb_\w+)\s*\(", text, flags=re.M):
+        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(fas_\w+|ns_\w+|fasb_\w+|gg_\w+)\s*\(", text, flags=re.M):
             names.add(m.group(1))
     return names
 

@@ -44,7 +44,7 @@ typedef enum {
   FAS_ENOMEM = 2,        /* device or host allocation failed                                  */
   FAS_ENOTCONV = 3,      /* kmax cycles done without reaching tol; info is filled            */
   FAS_ENONFINITE = 4,    /* residual became NaN/Inf                                           */
-  FAS_ETIMEOUT = 5,      /* a bounded device-side wait expired                               */
+  FAS_ETIMEOUT = 5,      /* a bounded device-side wait expired (fas_debug_bounded_wait)       */
   FAS_ECUDA = 6,         /* a CUDA runtime call failed (message in fas_last_error)            */
   FAS_EUNSUPPORTED = 7   /* valid request this build does not implement                       */
 } fas_status;
@@ -310,6 +310,14 @@ fas_status fas_selftest_conversions(long long count, unsigned long long seed, lo
  * denominator of the roofline of the float64 kernels. Runs on the current device and stream 0 and
  * waits for it; FAS_ECUDA if a CUDA call fails. */
 fas_status fas_probe_fp64_rate(double* tflops);
+
+/* Test hook of the bounded device waits (no counterpart in the paper). The 3D refinement residual
+ * streams its planes into shared memory with TMA tile copies and waits for each on an mbarrier; a
+ * wait gives up after limit_ns nanoseconds (default 1e9), the kernel stops its work and sets an error
+ * word, and the call that launched it returns FAS_ETIMEOUT (the context stays usable). limit_ns sets
+ * that deadline for later launches; withhold_next != 0 makes the next launch of that kernel withhold
+ * one copy (the first of block 0), so that its waits run out. Process-wide; FAS_EINVAL if limit_ns <= 0. */
+fas_status fas_debug_bounded_wait(long long limit_ns, int withhold_next);
 
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char* fas_last_error(void);

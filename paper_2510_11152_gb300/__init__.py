@@ -24,7 +24,7 @@ __all__ = [
     "fas_smooth", "fas_restrict", "fas_prolong_add", "fas_last_error", "fas_launch_count", "Solver",
     "fas_prof_enable", "fas_prof_read", "make_params", "fas_vcycle_small_static", "fas_solve_batched",
     "fas_autotune", "fas_heat_adjoint", "fas_fold_dirichlet", "solve", "HeatSolve", "fas_probe_fp64_rate",
-    "gg_model", "gg_create", "gg_step", "gg_rhs", "gg_destroy",
+    "gg_model", "gg_create", "gg_step", "gg_rhs", "gg_destroy", "fas_debug_bounded_wait",
 ]
 
 FAS_OK, FAS_EINVAL, FAS_ENOMEM, FAS_ENOTCONV, FAS_ENONFINITE, FAS_ETIMEOUT, FAS_ECUDA, FAS_EUNSUPPORTED = range(8)
@@ -119,6 +119,7 @@ def load(path: str | None = None):
         "fas_fold_dirichlet": (_I, [_P, _P, ctypes.POINTER(_D)]),
         "fas_selftest_conversions": (_I, [ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)]),
         "fas_probe_fp64_rate": (_I, [ctypes.POINTER(_D)]),
+        "fas_debug_bounded_wait": (_I, [ctypes.c_longlong, _I]),
         "ns_create": (_I, [_I, ctypes.POINTER(_I), _D, _D, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(fas_params),
                            ctypes.POINTER(fas_params), _P, ctypes.POINTER(_P)]),
         "ns_projection_step": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(fas_info),
@@ -301,6 +302,12 @@ def fas_probe_fp64_rate() -> float:
     out = ctypes.c_double(0.0)
     _check(load().fas_probe_fp64_rate(ctypes.byref(out)), "fas_probe_fp64_rate")
     return out.value
+
+
+def fas_debug_bounded_wait(limit_ns: int, withhold_next: bool = False) -> None:
+    """Deadline of the kernels' bounded waits, and the test hook that withholds one copy of the next
+    launch of the 3D refinement residual (its waits then run out: FAS_ETIMEOUT)."""
+    _check(load().fas_debug_bounded_wait(int(limit_ns), 1 if withhold_next else 0), "fas_debug_bounded_wait")
 
 
 def fas_smooth(ctx: _Ctx, level: int, u, f, sweeps: int) -> None:

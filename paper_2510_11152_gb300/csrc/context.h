@@ -74,8 +74,9 @@ struct fas_ctx {
   double* partials = nullptr;  // per-block partial sums
   int max_blocks = 0;
   double* d_scalar = nullptr;  // small device scalars
-  unsigned* ir_ticket = nullptr;  // work counter and finished-block count of the refinement residual
+  unsigned* ir_ticket = nullptr;  // refinement residual: work counter, finished blocks, timeout word
   double* h_scalar = nullptr;  // pinned host mirror
+  unsigned* h_flag = nullptr;  // pinned: the timeout word of ir_ticket read back after a solve
   double* b = nullptr;         // heat-step right-hand side (fine, float64)
   double* fproj = nullptr;     // mean-free copy of f for singular problems
   std::vector<double*> adj;     // adjoint buffers: checkpoints, segment states, lambda, mu, work

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <cmath>
 #include <cstdio>
@@ -19,12 +20,18 @@
 #include "context.h"
 #include "ir_strip.h"
 #include "stream2d.h"
+#include "tma.cuh"
 
 using namespace fasmg;
 
 namespace {
 
 thread_local std::string g_last_error;
+
+// Bounded waits of the tile copies (the 3D refinement residual): the deadline of one wait, and the
+// test hook that withholds one copy of the next launch (fas_debug_bounded_wait).
+std::atomic<unsigned long long> g_wait_limit_ns{kTmaWaitNs};
+std::atomic<int> g_withhold_copy{0};
 
 fas_status fail(fas_status s, const std::string& msg) {
   g_last_error = msg;
@@ -633,8 +640,10 @@ int launch_ir_residual(fas_ctx* c, float* r32, const double* u, const double* b,
   const int64_t n = c->shape[0].cells();
   int g = grid_for(c, n);
   Prof pr(c, FAS_K_IR, 0, (double)n);
-  if (ir_strip_supported(L))
-    launch_ir_strip(r32, u, b, L, nsp, c->partials, c->ir_ticket, c->sm_count, c->max_blocks, &g, c->stream);
+  if (ir_strip_supported(L) &&
+      launch_ir_strip(r32, u, b, L, nsp, c->partials, c->ir_ticket, c->sm_count, c->max_blocks, &g, c->stream,
+                      Ir3Wait{g_wait_limit_ns.load(), g_withhold_copy.exchange(0)}) == cudaSuccess)
+    ;  // the strip kernels took the level
   else if (c->p.dim == 2)
     k_ir_residual<2><<<g, kBlock, 0, c->stream>>>(r32, u, b, L, nsp, c->partials);
   else
@@ -726,11 +735,27 @@ fas_status enqueue_body(fas_ctx* c, double* u, const double* f_in, cudaGraphCond
   return FAS_OK;
 }
 
+// Enqueue the read-back of the refinement residual's timeout word (the host copy is valid after the
+// stream is synchronised; check_timeout reads it).
+cudaError_t enqueue_timeout_read(fas_ctx* c, cudaStream_t st) {
+  return cudaMemcpyAsync(c->h_flag, c->ir_ticket + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+}
+
+// FAS_ETIMEOUT (and the word cleared) when a bounded wait of a kernel ran out since the last check.
+fas_status check_timeout(fas_ctx* c, cudaStream_t st) {
+  if (*c->h_flag == 0u) return FAS_OK;
+  *c->h_flag = 0u;
+  CUDA_TRY(cudaMemsetAsync(c->ir_ticket + 2, 0, sizeof(unsigned), st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return fail(FAS_ETIMEOUT, "a bounded wait for a tile copy ran out in the refinement residual");
+}
+
 fas_status read_state(fas_ctx* c) {
   CUDA_TRY(cudaMemcpyAsync(c->Sh, c->S, sizeof(SolveState), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(enqueue_timeout_read(c, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   CUDA_TRY(cudaGetLastError());
-  return FAS_OK;
+  return check_timeout(c, c->stream);
 }
 
 fas_status finish_info(fas_ctx* c, fas_info* info, int max_cycles) {
@@ -1307,9 +1332,11 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
   };
   if (cudaMalloc(&c->partials, c->max_blocks * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "partials"));
   if (cudaMalloc(&c->d_scalar, 8 * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "scalars"));
-  if (cudaMalloc(&c->ir_ticket, 2 * sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(c->ir_ticket, 0, 2 * sizeof(unsigned)) != cudaSuccess)
+  if (cudaMalloc(&c->ir_ticket, 4 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(c->ir_ticket, 0, 4 * sizeof(unsigned)) != cudaSuccess)
     return bail(fail(FAS_ENOMEM, "work counter"));
+  if (cudaMallocHost(&c->h_flag, sizeof(unsigned)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "pinned flag"));
+  *c->h_flag = 0u;
   if (cudaMallocHost(&c->h_scalar, 8 * sizeof(double)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "pinned"));
   if (cudaMalloc(&c->S, sizeof(SolveState)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "solve state"));
   if (cudaMallocHost(&c->Sh, sizeof(SolveState)) != cudaSuccess) return bail(fail(FAS_ENOMEM, "pinned state"));
@@ -1327,6 +1354,7 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
     return bail(fail(FAS_ENOMEM, "fproj"));
   // kernel attributes, set before any launch or stream capture
   cudaError_t e = stream2d_prepare();
+  if (e == cudaSuccess) e = ir_strip_prepare();
   for (cudaError_t ek : {coarse_attr<double, 2>(), coarse_attr<double, 3>(), coarse_attr<float, 2>(),
                          coarse_attr<float, 3>()})
     if (e == cudaSuccess) e = ek;
@@ -1346,6 +1374,7 @@ fas_status fas_destroy(fas_ctx* c) {
   if (c->d_scalar) cudaFree(c->d_scalar);
   if (c->ir_ticket) cudaFree(c->ir_ticket);
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
+  if (c->h_flag) cudaFreeHost(c->h_flag);
   if (c->b) cudaFree(c->b);
   if (c->fproj) cudaFree(c->fproj);
   destroy_graphs(c);
@@ -1588,9 +1617,11 @@ fas_status fas_solve_batched(fas_ctx* const* ctxs, int count, double* const* u, 
   cudaStream_t st_ = (cudaStream_t)stream;
   CUDA_TRY(cudaGraphLaunch(B->exec, st_));
   CUDA_TRY(cudaMemcpyAsync(B->h_states, B->d_states, count * sizeof(SolveState), cudaMemcpyDeviceToHost, st_));
+  for (int i = 0; i < count; ++i) CUDA_TRY(enqueue_timeout_read(ctxs[i], st_));
   CUDA_TRY(cudaStreamSynchronize(st_));
   CUDA_TRY(cudaGetLastError());
   fas_status worst = FAS_OK;
+  for (int i = 0; i < count; ++i) STATUS_TRY(check_timeout(ctxs[i], st_));
   for (int i = 0; i < count; ++i) {
     fas_ctx* c = ctxs[i];
     *c->Sh = B->h_states[i];
@@ -1700,8 +1731,10 @@ fas_status fas_residual_ir(fas_ctx* c, const double* u, const double* f, float* 
     Prof pr(c, FAS_K_NORM, 0, 0.0);
     k_finish_norm<<<1, kBlock, 0, c->stream>>>(c->partials, g, c->d_scalar, nullptr);
   }
+  CUDA_TRY(enqueue_timeout_read(c, c->stream));
   double v = 0.0;
   STATUS_TRY(sync_read(c, &v));
+  STATUS_TRY(check_timeout(c, c->stream));
   if (norm2) *norm2 = v;
   return FAS_OK;
 }
@@ -1810,6 +1843,13 @@ fas_status fas_prof_read(fas_ctx* c, fas_prof_record* out, int cap, int* count) 
   }
   if (count) *count = (int)agg.size();
   for (int k = 0; k < (int)agg.size() && k < cap && out; ++k) out[k] = agg[k];
+  return FAS_OK;
+}
+
+fas_status fas_debug_bounded_wait(long long limit_ns, int withhold_next) {
+  if (limit_ns <= 0) return fail(FAS_EINVAL, "fas_debug_bounded_wait: limit_ns must be positive");
+  g_wait_limit_ns = (unsigned long long)limit_ns;
+  g_withhold_copy = withhold_next ? 1 : 0;
   return FAS_OK;
 }
 

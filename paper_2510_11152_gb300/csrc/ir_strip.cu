@@ -9,17 +9,21 @@
 // becomes r = fma(c, S, fma(-alpha, u, b)) (bits64.cuh). One warp owns a strip of 128 columns (four
 // per lane) and walks a segment of rows (2D) or planes (3D) keeping the neighbouring ones unpacked in
 // registers; horizontal neighbours come from the adjacent lanes, the strip's outer neighbours from
-// two extra loads. Windows whose values span more than 2^kMaxExpSpread in magnitude, or hold a
-// subnormal or non-finite value (2D: also a zero or values of both signs), take the float64 point
-// equation instead (the warp decides per row).
+// two extra loads. Windows whose values span more than 2^kMaxExpSpread in magnitude, or hold a zero,
+// a subnormal or non-finite value or values of both signs, take the float64 point equation instead
+// (2D: the warp decides per row; 3D: each lane for its four cells).
 #include <cuda_runtime.h>
+
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "bits64.cuh"
 #include "common.cuh"
 #include "ir_strip.h"
+#include "tma.cuh"
 
 namespace fasmg {
 namespace {
@@ -31,7 +35,6 @@ constexpr int kIrCpl2D = 4;   // cells per lane of the 2D kernel
 constexpr int kIrMinBlocks2D = 2;
 constexpr int kIrTasksPerWarp = 6;  // 2D work items per warp, taken dynamically
 constexpr unsigned kAll = 0xffffffffu;
-constexpr int kExpNone = 1 << 20;  // neutral bounds of an absent row; -kExpNone marks a bad value
 
 // The same row as loaded from memory (bit patterns), before unpacking.
 template <int CPL>
@@ -51,15 +54,6 @@ struct IrRowM {
   int kmin, kmax;   // warp-wide min / max of key = (sign << 11) | E over the row and its halo
 };
 constexpr int kKeyNone = 1 << 20;  // kmin of an absent row (kmax: -1)
-
-// The bit pattern of a normal float64 from its unpacked form.
-__device__ __forceinline__ uint64_t repack(int64_t sig, int E) {
-  const uint64_t neg = sig < 0 ? 1ull : 0ull;
-  const uint64_t m = neg ? (uint64_t)(-sig) : (uint64_t)sig;
-  return (neg << 63) | ((uint64_t)E << 52) | (m & kMant52);
-}
-
-__device__ __forceinline__ bool bad_exp(int E) { return (unsigned)(E - 1) >= 2046u; }
 
 __device__ __forceinline__ double as_d(uint64_t v) { return __longlong_as_double((long long)v); }
 
@@ -355,76 +349,127 @@ __global__ void __launch_bounds__(kIrThreads, MINB)
 }
 
 // ------------------------------------------------------------------------------------------------
-// 3D (cell-centred or face grids, constant kappa): a warp owns a 128-column strip of one row y and
-// walks a segment of planes z with the planes z-1, z, z+1 of its row unpacked in registers; the rows
-// y-1 and y+1 of the current plane are read by the neighbouring warps of the block too (eight
-// consecutive rows per block), so they come from L1. Exact zeros (the wall slots of face grids, a
-// fluid at rest) are exact values here: significand 0, outside the exponent range. Each lane decides
-// for its own four cells whether their stencils' values (its window of 22) qualify for the exact
-// sum: a 3D row of 128 cells of a smooth field spans more than 2^5 far more often than that.
+// 3D (cell-centred or face grids, constant kappa): a block of eight warps owns a 128-column strip of
+// eight consecutive rows y and walks a segment of planes z. The planes arrive in shared memory by TMA
+// tile loads, up to three planes ahead: per plane a tile of 10 rows (y0-1 .. y0+8) by 132 columns
+// (x0-2 .. x0+129; out-of-range cells read as zero) of u, in a ring of four slots, and the block's
+// 8 x 128 cells of b, in a ring of three, each slot with an mbarrier that the copies complete; every
+// wait on them is bounded (FAS_ETIMEOUT when a deadline passes).
+//
+// Every u value is unpacked once. Warp w owns row y0 + w; lane L owns its four cells x0 .. x0+3. When
+// plane z+1 arrives, each lane takes the bit patterns of its four cells (and of their left and right
+// neighbours) and turns them into signed significands aligned to the smallest exponent among them,
+// its "row reference" (exact zeros count as 0 and take no part in the exponent range). The aligned
+// row stays in the lane's registers for the planes z+1, z, z-1 of its own row, and goes to shared
+// memory (three plane buffers) for the warps of the rows y-1 and y+1; warps 0 and 7 also unpack the
+// tile's halo rows. The stencil of a cell then combines five rows, each already aligned to its own
+// reference: with Eref the smallest of the five references and every exponent within kMaxExpSpread
+// binades of it, each row's contribution is shifted left by (its reference - Eref) and
+// S = sum_nb u_nb - M u_c is exact in 64-bit integers; it is rounded once, and
+// r = fma(c, S, fma(-alpha, u, b)). A neighbour outside the grid takes the centre's own value in its
+// slot and counts once more in M (M = 6 inside the grid; at a boundary the diagonal's multiplicity mt
+// plus the number of absent neighbours). Windows with a subnormal or non-finite value or a wider
+// exponent range take the float64 point equation, from u in memory.
 // ------------------------------------------------------------------------------------------------
-constexpr int kIr3Rows = kIrWarps;  // rows y per block
+constexpr int kIr3Rows = kIrWarps;           // rows y per block
+constexpr int kU3W = kIrCols + 4;            // u tile row: x0-2 .. x0+129
+constexpr int kU3H = kIr3Rows + 2;           // u tile rows: y0-1 .. y0+8
+constexpr int kU3Vals = kU3W * kU3H;         // 1320 values, 10560 bytes
+constexpr int kU3Slot = 1328;                // slot stride in values (a multiple of 128 bytes)
+constexpr int kB3Slot = kIrCols * kIr3Rows;  // 1024 values
+constexpr int kDepthU = 4;                   // u tile slots: planes z-1 .. z+2 around the computed plane z
+constexpr int kDepth = 3;                    // b tile slots and aligned-row buffers
+constexpr int kA3Slot = kU3H * kIrCols;      // aligned rows of one plane: 10 x 128 int64
+constexpr int kRefNone = 1 << 20;            // reference of a row holding only zeros
+constexpr size_t kIr3Smem = (size_t)(kDepthU * kU3Slot + kDepth * kB3Slot) * sizeof(double) +
+                            (size_t)kDepth * kA3Slot * sizeof(int64_t) +
+                            (size_t)kDepth * kU3H * 32 * sizeof(int2) +      // per lane and row: reference, top
+                            (kDepthU + kDepth) * sizeof(uint64_t) + 128;     // barriers, alignment
 
-struct IrRow3 {
-  int64_t sig[4];
-  int E[4];
-  uint64_t halo;
-  int lo, hi;
-  bool present;
+__device__ __forceinline__ uint32_t hiw(uint64_t v) { return (uint32_t)(v >> 32); }
+
+// An aligned row of a lane: four signed significands times 2^(E - ref), the reference ref (the
+// smallest exponent among the unpacked values; kRefNone when all are zero, -kRefNone when one is
+// subnormal or non-finite) and the largest exponent top.
+struct ARow {
+  int64_t v[4];
+  int ref, top;
 };
 
-__device__ __forceinline__ void unpack_z(uint64_t raw, int64_t& sig, int& E, int& lo, int& hi, bool& bad) {
-  E = (int)((raw >> 52) & 0x7FF);
-  const bool zero = (raw << 1) == 0ull;
-  const int64_t m = (int64_t)((raw & kMant52) | (1ull << 52));
-  sig = zero ? 0 : ((raw >> 63) ? -m : m);
-  if (!zero) {
-    lo = min(lo, E);
-    hi = max(hi, E);
-    bad = bad || bad_exp(E);
-  }
+__device__ __forceinline__ void exp_range(uint64_t v, int& lo, int& hi) {
+  const int E = (int)((hiw(v) >> 20) & 0x7FFu);
+  const bool zero = (v << 1) == 0ull;
+  const bool bad = !zero && (unsigned)(E - 1) >= 2046u;
+  lo = bad ? -kRefNone : (zero ? lo : min(lo, E));
+  hi = zero ? hi : max(hi, E);
 }
 
-// sig 2^(E - Eref); zeros (sig 0) give 0 whatever their exponent field
-__device__ __forceinline__ int64_t align_z(int64_t sig, int E, int Eref) {
-  return (int64_t)((uint64_t)sig << ((E - Eref) & 63));
+// v m for a small m (a power of two: a left shift) as a 64 x 32-bit multiplication on the integer
+// multiply-add pipe instead of shifts on the ALU pipe (two's complement: also for negative v)
+__device__ __forceinline__ int64_t mul_u32(int64_t v, uint32_t m) {
+  const uint64_t lo = (uint64_t)(uint32_t)v * m;
+  const uint32_t hi = (uint32_t)((uint64_t)v >> 32) * m + (uint32_t)(lo >> 32);
+  return (int64_t)(((uint64_t)hi << 32) | (uint32_t)lo);
 }
 
-__device__ __forceinline__ void load_row3(IrRow3& R, const double* __restrict__ u, int64_t base, bool present,
-                                          int x0, int nx, int lane, bool halos) {
-  R.present = present;
-  int lo = kExpNone, hi = -kExpNone;
-  bool bad = false;
-  R.halo = 0ull;
-  if (present) {
-    const double2 a = reinterpret_cast<const double2*>(u + base)[0];
-    const double2 b = reinterpret_cast<const double2*>(u + base)[1];
-    const uint64_t v[4] = {(uint64_t)__double_as_longlong(a.x), (uint64_t)__double_as_longlong(a.y),
-                           (uint64_t)__double_as_longlong(b.x), (uint64_t)__double_as_longlong(b.y)};
+// The signed significand of the finite float64 with bit pattern v (0 for a zero), times 2^(E - ref),
+// for E - ref in 0..31.
+__device__ __forceinline__ int64_t sig_at(uint64_t v, int ref) {
+  const uint32_t h = hiw(v), l = (uint32_t)v;
+  const uint32_t m = (h & 0xFFFFFu) | 0x100000u;
+  const int sh = (int)((h >> 20) & 0x7FFu) - ref;
+  int64_t X = mul_u32((int64_t)(((uint64_t)m << 32) | l), 1u << (sh & 31));
+  X = (v << 1) == 0ull ? 0 : X;
+  const int64_t neg = (int64_t)((int32_t)h >> 31);  // 0 or -1
+  return (X ^ neg) - neg;
+}
+
+__device__ __forceinline__ void lds_raw4(uint64_t (&v)[4], const double* p) {  // p 16-byte aligned
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 c = reinterpret_cast<const double2*>(p)[1];
+  v[0] = (uint64_t)__double_as_longlong(a.x);
+  v[1] = (uint64_t)__double_as_longlong(a.y);
+  v[2] = (uint64_t)__double_as_longlong(c.x);
+  v[3] = (uint64_t)__double_as_longlong(c.y);
+}
+
+// Align a lane's four values (and, when given, the two horizontal neighbours) to their reference.
+__device__ __forceinline__ void align_row(ARow& R, const uint64_t (&v)[4], const uint64_t* wl, const uint64_t* er,
+                                          int64_t* aw, int64_t* ae) {
+  int lo = kRefNone, hi = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) unpack_z(v[k], R.sig[k], R.E[k], lo, hi, bad);
-    if (halos && ((lane == 0 && x0 > 0) || (lane == 31 && x0 + 4 < nx))) {
-      R.halo = (uint64_t)__double_as_longlong(u[lane == 0 ? base - 1 : base + 4]);
-      int64_t hs;
-      int Eh;
-      unpack_z(R.halo, hs, Eh, lo, hi, bad);
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      R.sig[k] = 0;
-      R.E[k] = 0;
-    }
+  for (int k = 0; k < 4; ++k) exp_range(v[k], lo, hi);
+  if (wl) {
+    exp_range(*wl, lo, hi);
+    exp_range(*er, lo, hi);
   }
-  R.lo = bad ? -kExpNone : lo;  // this lane's values only: the exact path is decided per lane
-  R.hi = hi;
+  R.ref = lo;
+  R.top = hi;
+  const int ref = lo < 1 ? 1 : (lo == kRefNone ? 1 : lo);  // any shift works for zeros; bad rows are unused
+#pragma unroll
+  for (int k = 0; k < 4; ++k) R.v[k] = sig_at(v[k], ref);
+  if (wl) {
+    *aw = sig_at(*wl, ref);
+    *ae = sig_at(*er, ref);
+  }
 }
 
 __global__ void __launch_bounds__(kIrThreads, 2)
-    k_ir_strip3(float* __restrict__ r32, const double* __restrict__ u, const double* __restrict__ b,
-                LevelDesc<double> L, const float* nsp, double* partials, int zseg) {
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
+    k_ir_strip3(float* __restrict__ r32, const double* __restrict__ u, const __grid_constant__ CUtensorMap tu,
+                const __grid_constant__ CUtensorMap tb, LevelDesc<double> L, const float* nsp, double* partials,
+                unsigned* ticket, int zseg, Ir3Wait wt) {
+  extern __shared__ __align__(128) unsigned char smem3[];
+  // the rings start on a 128-byte boundary (tile copies land on 128-byte aligned slots)
+  double* su = reinterpret_cast<double*>(smem3 + ((128u - (smem_u32(smem3) & 127u)) & 127u));
+  double* sb = su + kDepthU * kU3Slot;
+  int64_t* sa = reinterpret_cast<int64_t*>(sb + kDepth * kB3Slot);  // aligned rows per plane
+  int2* sr = reinterpret_cast<int2*>(sa + kDepth * kA3Slot);          // (reference, top) per lane and row
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sr + kDepth * kU3H * 32);  // u slots, then b slots
+  constexpr int kNBar = kDepthU + kDepth;
+  __shared__ int s_task;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int64_t sy = nx, sz = (int64_t)nx * ny;
   const int nstrips = nx / kIrCols;
@@ -432,94 +477,191 @@ __global__ void __launch_bounds__(kIrThreads, 2)
   const int nzs = (nz + zseg - 1) / zseg;
   const int ntasks = nstrips * nyg * nzs;
   const float nscale = nsp ? *nsp : 1.f;
+  if (tid == 0) {
+    for (int k = 0; k < kNBar; ++k) mbar_init(bar + k, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint32_t par = 0u;   // per barrier: parity of the phase this thread waits for next
+  uint32_t pend = 0u;  // thread 0: barriers with a copy issued and not yet waited for
+  bool aborted = false;
+  bool first_task = true;
   float acc = 0.f;
-  for (int task = blockIdx.x; task < ntasks; task += gridDim.x) {
+  auto wait_bar = [&](int k) -> bool {
+    const bool ok = mbar_wait_bounded(bar + k, (par >> k) & 1u, wt.limit_ns);
+    par ^= 1u << k;
+    if (tid == 0 && ok) pend &= ~(1u << k);
+    return ok;
+  };
+  while (!aborted) {
+    if (tid == 0) s_task = (int)atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int task = s_task;
+    __syncthreads();  // every thread has read s_task before it is written again
+    if (task >= ntasks) break;
     const int sx = task % nstrips;
     const int rest = task / nstrips;
-    const int y = (rest % nyg) * kIr3Rows + warp;
+    const int y0 = (rest % nyg) * kIr3Rows;
+    const int y = y0 + warp;
     const int z0 = (rest / nyg) * zseg, z1 = min(nz, z0 + zseg);
-    const int x0 = sx * kIrCols + 4 * lane;
-    const int64_t rowb = (int64_t)y * sy + x0;
-    IrRow3 P, C, N;
-    load_row3(P, u, rowb + (int64_t)(z0 - 1) * sz, z0 - 1 >= 0, x0, nx, lane, true);
-    load_row3(C, u, rowb + (int64_t)z0 * sz, true, x0, nx, lane, true);
+    const int xs = sx * kIrCols;
+    const int x0 = xs + 4 * lane;
+    auto issue_u = [&](int z) {
+      const int k = z % kDepthU;
+      mbar_expect_tx(bar + k, kU3Vals * (uint32_t)sizeof(double));
+      tma_load_3d(su + k * kU3Slot, &tu, xs - 2, y0 - 1, z, bar + k);
+      pend |= 1u << k;
+    };
+    auto issue_b = [&](int z) {
+      const int k = kDepthU + z % kDepth;
+      mbar_expect_tx(bar + k, kB3Slot * (uint32_t)sizeof(double));
+      tma_load_3d(sb + (z % kDepth) * kB3Slot, &tb, xs, y0, z, bar + k);
+      pend |= 1u << k;
+    };
+    // unpack plane z from its tile: this warp's row (with horizontal neighbours) into registers and
+    // the plane's aligned-row buffer; warps 0 and 7 also the tile's halo rows y0-1 and y0+8
+    auto unpack_plane = [&](int z, ARow& R, int64_t& aw, int64_t& ae) {
+      const double* T = su + (z % kDepthU) * kU3Slot;
+      int64_t* A = sa + (z % kDepth) * kA3Slot;
+      int2* Rf = sr + (z % kDepth) * kU3H * 32;
+      uint64_t v[4];
+      const double* row = T + (warp + 1) * kU3W + 4 * lane + 2;
+      lds_raw4(v, row);
+      uint64_t wl = (uint64_t)__double_as_longlong(row[-1]), er = (uint64_t)__double_as_longlong(row[4]);
+      if (x0 == 0) wl = v[0];  // absent: the centre's value
+      if (x0 + 4 == nx) er = v[3];
+      align_row(R, v, &wl, &er, &aw, &ae);
+      longlong2* dst = reinterpret_cast<longlong2*>(A + (warp + 1) * kIrCols + 4 * lane);
+      dst[0] = make_longlong2(R.v[0], R.v[1]);
+      dst[1] = make_longlong2(R.v[2], R.v[3]);
+      Rf[(warp + 1) * 32 + lane] = make_int2(R.ref, R.top);
+      if ((warp == 0 && y0 > 0) || (warp == kIr3Rows - 1 && y0 + kIr3Rows < ny)) {
+        const int hr = warp == 0 ? 0 : kU3H - 1;
+        ARow H;
+        lds_raw4(v, T + hr * kU3W + 4 * lane + 2);
+        align_row(H, v, nullptr, nullptr, nullptr, nullptr);
+        longlong2* hd = reinterpret_cast<longlong2*>(A + hr * kIrCols + 4 * lane);
+        hd[0] = make_longlong2(H.v[0], H.v[1]);
+        hd[1] = make_longlong2(H.v[2], H.v[3]);
+        Rf[hr * 32 + lane] = make_int2(H.ref, H.top);
+      }
+    };
+    // the test hook withholds one copy (block 0, first task): its waits must run out
+    const bool withhold = wt.withhold && blockIdx.x == 0 && first_task;
+    first_task = false;
+    if (tid == 0) {
+      fence_async_smem();  // the previous task's reads of the slots come before the new copies
+      if (z0 > 0) issue_u(z0 - 1);
+      if (!withhold) issue_u(z0);
+      if (z0 + 1 < nz) issue_u(z0 + 1);
+      issue_b(z0);
+      if (z0 + 1 < z1) issue_b(z0 + 1);
+    }
+    ARow P, C, N;
+    int64_t cw = 0, ce = 0, nw = 0, ne = 0, dw, de;
+    bool ok = true;
+    if (z0 > 0) {
+      ok = wait_bar((z0 - 1) % kDepthU) && ok;
+      if (ok) unpack_plane(z0 - 1, P, dw, de);
+    }
+    ok = wait_bar(z0 % kDepthU) && ok;
+    if (ok) unpack_plane(z0, C, cw, ce);
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    if (z0 == 0) P = C;  // absent plane: the centre's values
+    if (tid == 0) {
+      fence_async_smem();
+      if (z0 + 2 < nz && z0 + 2 <= z1) issue_u(z0 + 2);
+    }
     for (int z = z0; z < z1; ++z) {
-      load_row3(N, u, rowb + (int64_t)(z + 1) * sz, z + 1 < nz, x0, nx, lane, true);
-      const int64_t cb = rowb + (int64_t)z * sz;
-      IrRow3 S, T;  // rows y-1 and y+1 of plane z
-      load_row3(S, u, cb - sy, y > 0, x0, nx, lane, false);
-      load_row3(T, u, cb + sy, y < ny - 1, x0, nx, lane, false);
-      const double2 b01 = reinterpret_cast<const double2*>(b + cb)[0];
-      const double2 b23 = reinterpret_cast<const double2*>(b + cb)[1];
-      const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
-      double r[4];
-      // The lane's window: its four cells in the five rows and their two horizontal neighbours (from
-      // the adjacent lanes, or the strip's outer neighbours on lanes 0 and 31), unpacked.
-      long long sw = __shfl_up_sync(kAll, (long long)C.sig[3], 1);
-      int ew = __shfl_up_sync(kAll, C.E[3], 1);
-      long long se = __shfl_down_sync(kAll, (long long)C.sig[0], 1);
-      int ee = __shfl_down_sync(kAll, C.E[0], 1);
-      if (lane == 0 || lane == 31) {
-        int64_t hs = 0;
-        int Eh = 0, l0 = 0, h0 = 0;
-        bool bd = false;
-        unpack_z(C.halo, hs, Eh, l0, h0, bd);  // 0 where the strip has no outer neighbour
-        if (lane == 0) {
-          sw = hs;
-          ew = Eh;
+      ok = true;
+      if (z + 1 < nz) {
+        ok = wait_bar((z + 1) % kDepthU) && ok;
+        if (ok) unpack_plane(z + 1, N, nw, ne);
+      }
+      ok = wait_bar(kDepthU + z % kDepth) && ok;
+      // the aligned rows of plane z+1 are complete; plane z-1 (tile and b) is no longer read. A wait
+      // that ran out anywhere in the block ends its work.
+      if (__syncthreads_or(!ok)) {
+        aborted = true;
+        break;
+      }
+      if (tid == 0) {
+        fence_async_smem();
+        if (z + 3 < nz && z + 3 <= z1) issue_u(z + 3);  // into the slot of plane z-1
+        if (z + 2 < z1) issue_b(z + 2);                 // into the slot of plane z-1
+      }
+      if (z + 1 >= nz) {  // absent plane: the centre's values
+        N = C;
+        nw = cw;
+        ne = ce;
+      }
+      // rows y-1 and y+1 of plane z (absent rows: the centre's values)
+      ARow S, T;
+      {
+        const int64_t* A = sa + (z % kDepth) * kA3Slot;
+        const int2* Rf = sr + (z % kDepth) * kU3H * 32;
+        if (y > 0) {
+          const longlong2* q = reinterpret_cast<const longlong2*>(A + warp * kIrCols + 4 * lane);
+          const longlong2 a = q[0], c = q[1];
+          S.v[0] = a.x, S.v[1] = a.y, S.v[2] = c.x, S.v[3] = c.y;
+          const int2 rt = Rf[warp * 32 + lane];
+          S.ref = rt.x, S.top = rt.y;
         } else {
-          se = hs;
-          ee = Eh;
+          S = C;
+        }
+        if (y < ny - 1) {
+          const longlong2* q = reinterpret_cast<const longlong2*>(A + (warp + 2) * kIrCols + 4 * lane);
+          const longlong2 a = q[0], c = q[1];
+          T.v[0] = a.x, T.v[1] = a.y, T.v[2] = c.x, T.v[3] = c.y;
+          const int2 rt = Rf[(warp + 2) * 32 + lane];
+          T.ref = rt.x, T.top = rt.y;
+        } else {
+          T = C;
         }
       }
-      int Eref = min(min(C.lo, min(P.lo, N.lo)), min(S.lo, T.lo));
-      int Etop = max(max(C.hi, max(P.hi, N.hi)), max(S.hi, T.hi));
-      if (sw != 0) {
-        Eref = bad_exp(ew) ? -kExpNone : min(Eref, ew);
-        Etop = max(Etop, ew);
-      }
-      if (se != 0) {
-        Eref = bad_exp(ee) ? -kExpNone : min(Eref, ee);
-        Etop = max(Etop, ee);
-      }
-      // an all-zero window has Eref = kExpNone: any exponent works, use 1
-      const int Eb = Eref == kExpNone ? 1 : Eref;
-      const bool want = Etop - Eref <= kMaxExpSpread || Eref == kExpNone;
-      bool ok = want;
-      if (want) {  // per lane; nothing below synchronises the warp
-        int64_t Xc[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) Xc[k] = align_z(C.sig[k], C.E[k], Eb);
-        const int64_t wl = align_z(sw, ew, Eb), er = align_z(se, ee, Eb);
+      const double* bp = sb + (z % kDepth) * kB3Slot + warp * kIrCols + 4 * lane;
+      const double2 b01 = reinterpret_cast<const double2*>(bp)[0];
+      const double2 b23 = reinterpret_cast<const double2*>(bp)[1];
+      const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
+      uint64_t craw[4];  // this row of plane z, still in its tile slot
+      lds_raw4(craw, su + (z % kDepthU) * kU3Slot + (warp + 1) * kU3W + 4 * lane + 2);
+      const int eref = min(min(C.ref, min(P.ref, N.ref)), min(S.ref, T.ref));
+      const int etop = max(max(C.top, max(P.top, N.top)), max(S.top, T.top));
+      double r[4];
+      bool ex = eref >= 1 && etop <= 2046 && (eref == kRefNone || etop - eref <= kMaxExpSpread);
+      if (ex) {  // per lane; nothing below synchronises the warp
+        const int e0 = eref == kRefNone ? 1 : eref;
+        // each row's shift to the common reference (rows of zeros have any reference: shift 0)
+        auto msh = [&](const ARow& R) { return 1u << (R.ref == kRefNone ? 0 : (R.ref < 1 ? 1 : R.ref) - e0); };
+        const uint32_t mC = msh(C), mP = msh(P), mN = msh(N), mS = msh(S), mT = msh(T);
         const bool inner = y > 0 && y < ny - 1 && z > 0 && z < nz - 1;
-        int64_t Sx[4];
-        bool small = true;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const int64_t Xw = k ? Xc[k - 1] : wl;
-          const int64_t Xe = k < 3 ? Xc[k + 1] : er;
-          const int64_t V = (align_z(S.sig[k], S.E[k], Eb) + align_z(T.sig[k], T.E[k], Eb)) +
-                            (align_z(P.sig[k], P.E[k], Eb) + align_z(N.sig[k], N.E[k], Eb));
+          const int64_t sw = k ? C.v[k - 1] : cw;
+          const int64_t se = k < 3 ? C.v[k + 1] : ce;
           int M = 6;
           if (!inner || (k == 0 && x0 == 0) || (k == 3 && x0 + 4 == nx)) {
             const int cls = bclass<3>(x0 + k, y, z, nx, ny, nz);
-            M = (int)L.mt[cls];
+            M = (int)L.mt[cls] + __popc(cls);
           }
-          Sx[k] = (Xw + Xe) + V - (int64_t)M * Xc[k];
-          small = small && (uint64_t)(Sx[k] + ((1ll << 53) - 1)) < (1ull << 54) - 1ull;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
+          const int64_t cpart = (sw + se) - mul_u32(C.v[k], (uint32_t)M);
+          const int64_t sum = mul_u32(cpart, mC) + (mul_u32(P.v[k], mP) + mul_u32(N.v[k], mN)) +
+                              (mul_u32(S.v[k], mS) + mul_u32(T.v[k], mT));
           double Sd;
-          ok = (small ? fixed_to_f64_small(Sx[k], Eb, &Sd) : fixed_to_f64(Sx[k], Eb, &Sd)) && ok;
-          r[k] = fma(L.c, Sd, fma(-L.alpha, as_d(repack(C.sig[k], C.E[k])), bv[k]));
+          // |sum| < 2^53 (the usual case: S is a second difference) converts without rounding
+          const bool small = (uint64_t)(sum + ((1ll << 53) - 1)) < (1ull << 54) - 1ull;
+          ex = (small ? fixed_to_f64_small(sum, e0, &Sd) : fixed_to_f64(sum, e0, &Sd)) && ex;
+          r[k] = fma(L.c, Sd, fma(-L.alpha, as_d(craw[k]), bv[k]));
         }
       }
-      if (!ok) {  // the float64 point equation, as in residual_point, from the values in memory
+      if (!ex) {  // the float64 point equation, as in residual_point, from the values in memory
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int x = x0 + k;
-          const int64_t q = cb + k;
+          const int64_t q = (int64_t)z * sz + (int64_t)y * sy + x;
           const double w = x > 0 ? u[q - 1] : 0.0;
           const double e = x < nx - 1 ? u[q + 1] : 0.0;
           const double sv = y > 0 ? u[q - sy] : 0.0;
@@ -552,7 +694,7 @@ __global__ void __launch_bounds__(kIrThreads, 2)
         o.z = f64_to_f32_rn_bits(r[2]);
         o.w = f64_to_f32_rn_bits(r[3]);
       }
-      *reinterpret_cast<float4*>(r32 + cb) = o;
+      *reinterpret_cast<float4*>(r32 + (int64_t)z * sz + (int64_t)y * sy + x0) = o;
       const float s0 = o.x * nscale, s1 = o.y * nscale, s2 = o.z * nscale, s3 = o.w * nscale;
       acc = fmaf(s0, s0, acc);
       acc = fmaf(s1, s1, acc);
@@ -560,13 +702,53 @@ __global__ void __launch_bounds__(kIrThreads, 2)
       acc = fmaf(s3, s3, acc);
       P = C;
       C = N;
+      cw = nw;
+      ce = ne;
     }
   }
-  const double s = block_sum((double)acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  if (aborted && tid == 0) {
+    atomicOr(ticket + 2, 1u);  // the host reports FAS_ETIMEOUT
+    // copies still in flight must land before the block's shared memory is released
+    for (int k = 0; k < kNBar; ++k)
+      if ((pend >> k) & 1u) mbar_wait_bounded(bar + k, (par >> k) & 1u, wt.limit_ns);
+  }
+  const double s = block_sum((double)acc);  // every warp of the block has left the task loop
+  if (tid == 0) {
+    partials[blockIdx.x] = s;
+    __threadfence();
+    if (atomicAdd(ticket + 1, 1u) == gridDim.x - 1) {  // the last block: no block takes tasks any more
+      ticket[0] = 0u;
+      ticket[1] = 0u;
+    }
+  }
 }
 
 }  // namespace
+
+cudaError_t tensor_map_f64_3d(CUtensorMap* map, const double* base, int nx, int ny, int nz, int bx, int by, int bz) {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!encode) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(double), (cuuint64_t)nx * ny * sizeof(double)};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double*>(base), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t ir_strip_prepare() {
+  return cudaFuncSetAttribute(k_ir_strip3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIr3Smem);
+}
 
 bool ir_strip_supported(const LevelDesc<double>& L) {
   if (L.varkappa || L.per || L.nx % kIrCols != 0) return false;
@@ -576,17 +758,23 @@ bool ir_strip_supported(const LevelDesc<double>& L) {
 
 cudaError_t launch_ir_strip(float* r32, const double* u, const double* b, const LevelDesc<double>& L,
                             const float* nsp, double* partials, unsigned* ticket, int sm_count, int max_blocks,
-                            int* nblocks, cudaStream_t stream) {
+                            int* nblocks, cudaStream_t stream, Ir3Wait wt) {
   const int nstrips = L.nx / kIrCols;
   if (L.nz > 1) {
-    // blocks of eight rows y; z segments sized for about four blocks per SM, 8..128 planes each
+    // one wave of two blocks of eight rows y per SM taking (strip, row group, plane segment) tasks;
+    // segments of 16..128 planes (two halo planes each) sized for about kIrTasksPerWarp tasks per block
     const int64_t cols = (int64_t)nstrips * (L.ny / kIr3Rows);
-    const int64_t per = std::max<int64_t>(1, ((int64_t)sm_count * 4) / cols);
-    const int zseg = (int)std::min<int64_t>(128, std::max<int64_t>(8, (L.nz + per - 1) / per));
+    const int64_t wave = (int64_t)sm_count * 2;
+    const int64_t per = std::max<int64_t>(1, (wave * kIrTasksPerWarp + cols - 1) / cols);
+    const int zseg = (int)std::min<int64_t>(128, std::max<int64_t>(16, (L.nz + per - 1) / per));
     const int64_t ntasks = cols * ((L.nz + zseg - 1) / zseg);
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(max_blocks, ntasks));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(max_blocks, ntasks), wave));
+    CUtensorMap tu, tb;
+    cudaError_t e = tensor_map_f64_3d(&tu, u, L.nx, L.ny, L.nz, kU3W, kU3H, 1);
+    if (e == cudaSuccess) e = tensor_map_f64_3d(&tb, b, L.nx, L.ny, L.nz, kIrCols, kIr3Rows, 1);
+    if (e != cudaSuccess) return e;
     *nblocks = blocks;
-    k_ir_strip3<<<blocks, kIrThreads, 0, stream>>>(r32, u, b, L, nsp, partials, zseg);
+    k_ir_strip3<<<blocks, kIrThreads, kIr3Smem, stream>>>(r32, u, tu, tb, L, nsp, partials, ticket, zseg, wt);
     return cudaGetLastError();
   }
   // one wave of kIrMinBlocks2D blocks of eight warps per SM; segments of 16..256 rows (two halo rows

@@ -71,14 +71,16 @@ def test_checkpoint_interval_does_not_change_gradients(cuda_lib):
             np.testing.assert_array_equal(a, b)
 
 
-def test_full_workload_central_differences(cuda_lib):
-    """1024^2, 50 steps, kappa = 1 + 0.5 tanh(8 Gaussians), loss ||u_T - u_target||^2: directional
-    derivatives along random u0, f and kappa directions from the adjoint agree with central
-    differences of float64 runs to 1e-6 relative."""
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_workload_central_differences(cuda_lib, precision):
+    """1024^2, 50 steps, kappa = 1 + 0.5 tanh(8 Gaussians), loss ||u_T - u_target||^2, checkpoints
+    every 10 steps: directional derivatives along random u0, f and kappa directions from the adjoint
+    agree with central differences of forward runs to 1e-6 relative, with float64 solves and with
+    mixed-precision solves (forward runs and adjoint alike, each solve to 1e-12)."""
     fas = cuda_lib
     w = adjoint_heat()
     shape, h, dt, steps = w["shape"], w["h"], w["dt"], w["nsteps"]
-    opts = dict(beta=dt, coarsest=4, tol=1e-12, kmax=60)
+    opts = dict(beta=dt, coarsest=4, tol=1e-12, kmax=60, precision=precision)
 
     def run(u0, f, kappa):
         ctx = fas.fas_create(fas.make_params(shape, h, **opts), kappa=_t(kappa))

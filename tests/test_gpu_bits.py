@@ -175,3 +175,31 @@ def test_refinement_residual_is_reproducible(cuda_lib):
         nrm = fas.fas_residual_ir(ctx, ut, ft, r32)
         assert abs(nrm - first) <= 1e-9 * first
         assert torch.equal(r32, r_first)
+
+
+def test_bounded_wait_runs_out_and_context_stays_usable(cuda_lib):
+    """The 3D refinement residual waits for its tile copies with a deadline. With one copy withheld
+    (the test hook), the call returns FAS_ETIMEOUT after the deadline instead of waiting forever; the
+    next call on the same context gives the same residual as before, bit for bit, and a solve on the
+    context converges."""
+    import torch
+    fas = cuda_lib
+    shape = (32, 64, 128)
+    u = noisy_cos_mode(shape, 621) + 1.5
+    f = u + 1e-3 * random_field(shape, 622, -1, 1)
+    ctx = fas.fas_create(fas.make_params(shape, 1.0 / 128, alpha=1.0, beta=1e-3, precision=fas.FAS_MIXED, kmax=60))
+    ut, ft = _t(u), _t(f)
+    r32 = torch.empty(u.size, dtype=torch.float32, device="cuda")
+    n0 = fas.fas_residual_ir(ctx, ut, ft, r32)
+    r_ref = r32.clone()
+    fas.fas_debug_bounded_wait(20_000_000, withhold_next=True)  # 20 ms
+    try:
+        with pytest.raises(fas.FasError) as e:
+            fas.fas_residual_ir(ctx, ut, ft, r32)
+        assert e.value.status == fas.FAS_ETIMEOUT
+    finally:
+        fas.fas_debug_bounded_wait(1_000_000_000, withhold_next=False)
+    n1 = fas.fas_residual_ir(ctx, ut, ft, r32)
+    assert torch.equal(r32, r_ref) and abs(n1 - n0) <= 1e-9 * n0
+    x = _t(np.zeros(shape))
+    assert fas.fas_solve(ctx, x, ft).converged

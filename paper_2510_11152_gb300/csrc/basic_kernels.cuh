@@ -298,8 +298,8 @@ struct Quad<double> {
   }
 };
 
-template <typename T, int DIM>
-__global__ void k_smooth_colour4(T* u, const T* f, LevelDesc<T> L, int colour) {
+template <typename T, int DIM, bool PER>
+__device__ __forceinline__ void smooth_colour4_body(T* u, const T* f, const LevelDesc<T>& L, int colour) {
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int64_t sy = nx, sz = (int64_t)nx * ny;
   const int gpr = nx >> 2;  // groups per row
@@ -314,18 +314,14 @@ __global__ void k_smooth_colour4(T* u, const T* f, LevelDesc<T> L, int colour) {
     c.ld(u + idx);
     f4.ld(f + idx);
     // neighbours across a boundary: the wrapped cells on a periodic axis, none otherwise
-    const bool px = L.per & 1, py = (L.per >> 1) & 1, pz = (L.per >> 2) & 1;
-    const T wedge = x0 > 0 ? u[idx - 1] : (px ? u[idx + nx - 1] : T(0));
-    const T eedge = x0 + 4 < nx ? u[idx + 4] : (px ? u[idx + 4 - nx] : T(0));
-    if (j > 0) s4.ld(u + idx - sy);
-    else if (py) s4.ld(u + idx + (ny - 1) * sy);
-    if (j < ny - 1) n4.ld(u + idx + sy);
-    else if (py) n4.ld(u + idx - (ny - 1) * sy);
+    const bool px = PER && (L.per & 1), py = PER && ((L.per >> 1) & 1), pz = PER && ((L.per >> 2) & 1);
+    const T wedge = (x0 > 0 || px) ? u[x0 > 0 ? idx - 1 : idx + nx - 1] : T(0);
+    const T eedge = (x0 + 4 < nx || px) ? u[x0 + 4 < nx ? idx + 4 : idx + 4 - nx] : T(0);
+    if (j > 0 || py) s4.ld(u + (j > 0 ? idx - sy : idx + (ny - 1) * sy));
+    if (j < ny - 1 || py) n4.ld(u + (j < ny - 1 ? idx + sy : idx - (ny - 1) * sy));
     if (DIM == 3) {
-      if (l > 0) b4.ld(u + idx - sz);
-      else if (pz) b4.ld(u + idx + (nz - 1) * sz);
-      if (l < nz - 1) t4.ld(u + idx + sz);
-      else if (pz) t4.ld(u + idx - (nz - 1) * sz);
+      if (l > 0 || pz) b4.ld(u + (l > 0 ? idx - sz : idx + (nz - 1) * sz));
+      if (l < nz - 1 || pz) t4.ld(u + (l < nz - 1 ? idx + sz : idx - (nz - 1) * sz));
     }
     // cell x has the colour when (x + j + l + DIM + colour) is even; the same along a row
     auto upd = [&](auto kc) {
@@ -354,6 +350,14 @@ __global__ void k_smooth_colour4(T* u, const T* f, LevelDesc<T> L, int colour) {
     }
     c.st(u + idx);
   }
+}
+
+template <typename T, int DIM>
+__global__ void k_smooth_colour4(T* u, const T* f, LevelDesc<T> L, int colour) {
+  if (L.per)
+    smooth_colour4_body<T, DIM, true>(u, f, L, colour);
+  else
+    smooth_colour4_body<T, DIM, false>(u, f, L, colour);
 }
 
 // r (nullable) = f - A u; per-block partial of sum (s r)^2 into partials[blockIdx.x], s = *nsp (or 1).

@@ -62,22 +62,45 @@ __device__ __forceinline__ bool frozen(const LevelDesc<T>& L, int i, int j, int 
 }
 
 // Sum of the existing neighbours of cell (i, j, l) at linear index idx (constant kappa); on a periodic
-// axis (bit of per) the neighbour across the boundary is the wrapped cell.
-template <typename T, int DIM>
-__device__ __forceinline__ T nbsum(const T* __restrict__ u, int64_t idx, int i, int j, int l, int nx,
-                                   int ny, int nz, int per) {
+// axis (bit of per) the neighbour across the boundary is the wrapped cell. PER = false is the code for
+// levels without periodic axes.
+template <typename T, int DIM, bool PER>
+__device__ __forceinline__ T nbsum_t(const T* __restrict__ u, int64_t idx, int i, int j, int l, int nx, int ny,
+                                     int nz, int per) {
   const int64_t sy = nx, sz = (int64_t)nx * ny;
-  T w = i > 0 ? u[idx - 1] : ((per & 1) ? u[idx + nx - 1] : T(0));
-  T e = i < nx - 1 ? u[idx + 1] : ((per & 1) ? u[idx - (nx - 1)] : T(0));
-  T s = j > 0 ? u[idx - sy] : ((per & 2) ? u[idx + (ny - 1) * sy] : T(0));
-  T n = j < ny - 1 ? u[idx + sy] : ((per & 2) ? u[idx - (ny - 1) * sy] : T(0));
-  T acc = (w + e) + (s + n);
-  if (DIM == 3) {
-    T bo = l > 0 ? u[idx - sz] : ((per & 4) ? u[idx + (nz - 1) * sz] : T(0));
-    T to = l < nz - 1 ? u[idx + sz] : ((per & 4) ? u[idx - (nz - 1) * sz] : T(0));
-    acc = acc + (bo + to);
+  if constexpr (!PER) {
+    T w = i > 0 ? u[idx - 1] : T(0);
+    T e = i < nx - 1 ? u[idx + 1] : T(0);
+    T s = j > 0 ? u[idx - sy] : T(0);
+    T n = j < ny - 1 ? u[idx + sy] : T(0);
+    T acc = (w + e) + (s + n);
+    if (DIM == 3) {
+      T bo = l > 0 ? u[idx - sz] : T(0);
+      T to = l < nz - 1 ? u[idx + sz] : T(0);
+      acc = acc + (bo + to);
+    }
+    return acc;
+  } else {
+    // one load per neighbour: the address wraps on a periodic axis, the value is 0 where none exists
+    T w = (i > 0 || (per & 1)) ? u[i > 0 ? idx - 1 : idx + (nx - 1)] : T(0);
+    T e = (i < nx - 1 || (per & 1)) ? u[i < nx - 1 ? idx + 1 : idx - (nx - 1)] : T(0);
+    T s = (j > 0 || (per & 2)) ? u[j > 0 ? idx - sy : idx + (ny - 1) * sy] : T(0);
+    T n = (j < ny - 1 || (per & 2)) ? u[j < ny - 1 ? idx + sy : idx - (ny - 1) * sy] : T(0);
+    T acc = (w + e) + (s + n);
+    if (DIM == 3) {
+      T bo = (l > 0 || (per & 4)) ? u[l > 0 ? idx - sz : idx + (nz - 1) * sz] : T(0);
+      T to = (l < nz - 1 || (per & 4)) ? u[l < nz - 1 ? idx + sz : idx - (nz - 1) * sz] : T(0);
+      acc = acc + (bo + to);
+    }
+    return acc;
   }
-  return acc;
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ T nbsum(const T* __restrict__ u, int64_t idx, int i, int j, int l, int nx, int ny, int nz,
+                                   int per) {
+  return per ? nbsum_t<T, DIM, true>(u, idx, i, j, l, nx, ny, nz, per)
+             : nbsum_t<T, DIM, false>(u, idx, i, j, l, nx, ny, nz, 0);
 }
 
 // Weighted neighbour sum sum_f w_f u_nb (per-cell kappa).

@@ -20,6 +20,7 @@
 #include "context.h"
 #include "ir_strip.h"
 #include "stream2d.h"
+#include "stream3d.h"
 #include "tma.cuh"
 
 using namespace fasmg;
@@ -396,6 +397,13 @@ fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers)
       STATUS_TRY(dev_alloc(H, &H.u2[l], c->shape[l].cells()));
       if (l + 1 < H.nfast) STATUS_TRY(dev_alloc(H, &H.rc[l + 1], c->shape[l + 1].cells()));
     }
+    // sweep-fused 3D smoothing (float32): a second buffer on every level above the single-CTA level
+    // that the fused sweep handles (its sweeps ping-pong between the two)
+    if constexpr (std::is_same<T, float>::value) {
+      if (p.dim == 3 && p.path == 0 && p.ordering == FAS_ORDER_FORWARD && p.nu1 + p.nu2 >= 2)
+        for (int l = 0; l < H.switch_level; ++l)
+          if (sweep3d_supported(H.desc[l])) STATUS_TRY(dev_alloc(H, &H.u2[l], c->shape[l].cells()));
+    }
     T** arrs[3] = {nullptr, nullptr, nullptr};
     for (int k = 0; k < 3; ++k) STATUS_TRY(dev_alloc(H, &arrs[k], kMaxLevels));
     H.d_u = arrs[0];
@@ -458,12 +466,38 @@ void launch_prolong(fas_ctx* c, int64_t n, T* u, const T* uc, const T* uc0, int 
   });
 }
 
+// `sweeps` X-MCGS sweeps in place on u. With a scratch buffer of the level's size (3D float32 levels
+// the fused sweep handles), sweeps run in pairs through the sweep-fused kernel, u -> scratch -> u; an
+// odd last sweep, and every other level, runs one launch per colour phase.
 template <typename T, int DIM>
-void launch_smooth(fas_ctx* c, const LevelDesc<T>& L, int level, T* u, const T* f, int sweeps) {
+void launch_smooth(fas_ctx* c, const LevelDesc<T>& L, int level, T* u, const T* f, int sweeps, T* scratch = nullptr) {
   const int64_t half = (int64_t)(L.nx / 2) * L.ny * L.nz;
   const bool g4ok = !L.varkappa && L.nx % 4 == 0;  // 16-byte groups of 4 cells
   const int g = grid_for(c, g4ok ? half / 2 : half);
-  for (int s = 0; s < sweeps; ++s) {
+  int s0 = 0;
+  if constexpr (std::is_same<T, float>::value && DIM == 3) {
+    if (scratch && c->p.ordering == FAS_ORDER_FORWARD)
+      for (; s0 + 2 <= sweeps; s0 += 2) {
+        cudaError_t e;
+        {
+          Prof pr(c, FAS_K_SMOOTH, level, (double)(2 * half));
+          e = launch_sweep3d(scratch, u, f, L, first_colour(c->p.ordering, s0), c->sm_count, c->ir_ticket + 2,
+                             g_wait_limit_ns.load(), c->stream);
+        }
+        if (e != cudaSuccess) break;  // nothing was launched: the colour launches below do the sweeps
+        {
+          Prof pr(c, FAS_K_SMOOTH, level, (double)(2 * half));
+          e = launch_sweep3d(u, scratch, f, L, first_colour(c->p.ordering, s0 + 1), c->sm_count, c->ir_ticket + 2,
+                             g_wait_limit_ns.load(), c->stream);
+        }
+        if (e != cudaSuccess) {  // one sweep done, into scratch: bring it back
+          cudaMemcpyAsync(u, scratch, (size_t)(2 * half) * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
+          s0 += 1;
+          break;
+        }
+      }
+  }
+  for (int s = s0; s < sweeps; ++s) {
     const int c0 = first_colour(c->p.ordering, s);
     for (const int colour : {c0, 1 - c0}) {
       Prof pr(c, FAS_K_SMOOTH, level, (double)half);
@@ -522,7 +556,8 @@ fas_status vcycle_basic_from(fas_ctx* c, Hier<T>& H, int lfrom, T* utop, const T
     const LevelDesc<T>& L = H.desc[l];
     T* u = l == lfrom ? utop : H.u[l];
     const T* f = l == lfrom ? ftop : H.f[l];
-    launch_smooth<T, DIM>(c, L, l, u, f, p.nu1);
+    T* scratch = (DIM == 3 && l < (int)H.u2.size()) ? H.u2[l] : nullptr;  // fused 3D sweeps
+    launch_smooth<T, DIM>(c, L, l, u, f, p.nu1, scratch);
     const int64_t n = (int64_t)L.nx * L.ny * L.nz;
     const int64_t nc = n >> DIM;
     {  // residual and its restriction in one pass (the residual is not stored)
@@ -548,7 +583,7 @@ fas_status vcycle_basic_from(fas_ctx* c, Hier<T>& H, int lfrom, T* utop, const T
       Prof pr(c, FAS_K_PROLONG, l, (double)n);
       launch_prolong<T, DIM>(c, n, u, H.u[l + 1], H.u0[l + 1], L.nx, L.ny, L.nz);
     }
-    launch_smooth<T, DIM>(c, L, l, u, f, p.nu2);
+    launch_smooth<T, DIM>(c, L, l, u, f, p.nu2, (DIM == 3 && l < (int)H.u2.size()) ? H.u2[l] : nullptr);
   }
   return FAS_OK;
 }
@@ -1355,6 +1390,7 @@ fas_status fas_create(const fas_params* pin, void* stream, fas_ctx** out) {
   // kernel attributes, set before any launch or stream capture
   cudaError_t e = stream2d_prepare();
   if (e == cudaSuccess) e = ir_strip_prepare();
+  if (e == cudaSuccess) e = sweep3d_prepare();
   for (cudaError_t ek : {coarse_attr<double, 2>(), coarse_attr<double, 3>(), coarse_attr<float, 2>(),
                          coarse_attr<float, 3>()})
     if (e == cudaSuccess) e = ek;

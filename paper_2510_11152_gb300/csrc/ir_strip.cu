@@ -14,8 +14,6 @@
 // (2D: the warp decides per row; 3D: each lane for its four cells).
 #include <cuda_runtime.h>
 
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
@@ -725,27 +723,6 @@ __global__ void __launch_bounds__(kIrThreads, 2)
 
 }  // namespace
 
-cudaError_t tensor_map_f64_3d(CUtensorMap* map, const double* base, int nx, int ny, int nz, int bx, int by, int bz) {
-  static std::once_flag once;
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  std::call_once(once, [] {
-    cudaDriverEntryPointQueryResult q;
-    void* fn = nullptr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  });
-  if (!encode) return cudaErrorNotSupported;
-  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(double), (cuuint64_t)nx * ny * sizeof(double)};
-  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double*>(base), dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 cudaError_t ir_strip_prepare() {
   return cudaFuncSetAttribute(k_ir_strip3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIr3Smem);
 }
@@ -770,8 +747,8 @@ cudaError_t launch_ir_strip(float* r32, const double* u, const double* b, const 
     const int64_t ntasks = cols * ((L.nz + zseg - 1) / zseg);
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(max_blocks, ntasks), wave));
     CUtensorMap tu, tb;
-    cudaError_t e = tensor_map_f64_3d(&tu, u, L.nx, L.ny, L.nz, kU3W, kU3H, 1);
-    if (e == cudaSuccess) e = tensor_map_f64_3d(&tb, b, L.nx, L.ny, L.nz, kIrCols, kIr3Rows, 1);
+    cudaError_t e = tensor_map_3d(&tu, u, sizeof(double), L.nx, L.ny, L.nz, kU3W, kU3H, 1);
+    if (e == cudaSuccess) e = tensor_map_3d(&tb, b, sizeof(double), L.nx, L.ny, L.nz, kIrCols, kIr3Rows, 1);
     if (e != cudaSuccess) return e;
     *nblocks = blocks;
     k_ir_strip3<<<blocks, kIrThreads, kIr3Smem, stream>>>(r32, u, tu, tb, L, nsp, partials, ticket, zseg, wt);

@@ -77,8 +77,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// Host: a rank-3 tensor map of a dense float64 field (x fastest) with box (bx, by, bz). Returns
-// cudaErrorInvalidValue when the driver rejects the description (alignment, sizes).
-cudaError_t tensor_map_f64_3d(CUtensorMap* map, const double* base, int nx, int ny, int nz, int bx, int by, int bz);
+// Host: a rank-3 tensor map of a dense float64 or float32 field (elem_bytes 8 or 4, x fastest) with
+// box (bx, by, bz); out-of-range elements of a tile load read as zero. Returns cudaErrorInvalidValue
+// when the driver rejects the description (alignment, sizes), cudaErrorNotSupported without the
+// driver's entry point.
+cudaError_t tensor_map_3d(CUtensorMap* map, const void* base, int elem_bytes, int nx, int ny, int nz, int bx, int by,
+                          int bz);
 
 }  // namespace fasmg

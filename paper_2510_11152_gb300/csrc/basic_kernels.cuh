@@ -17,7 +17,7 @@ namespace fasmg {
 // paper's sets 1,2 in 2D, sets 1-4 in 3D); colour 0: even (sets 3,4 / 5-8). With the 0-based indices
 // used here the 1-based sum is the 0-based sum plus DIM. Every cell of a colour has only other-colour
 // neighbours, so all of them update at once from the current values.
-template <typename T, int DIM>
+template <typename T, int DIM, bool PER = false>
 __device__ __forceinline__ void smooth_colour_range(T* u, const T* f, const LevelDesc<T>& L, int colour,
                                                     int64_t t0, int64_t stride) {
   const int lhx = L.lx - 1;
@@ -29,12 +29,12 @@ __device__ __forceinline__ void smooth_colour_range(T* u, const T* f, const Leve
     const int i = 2 * k + ((colour + DIM + j + l) & 1);
     const int64_t idx = ((int64_t)l * L.ny + j) * L.nx + i;
     if (L.fax >= 0 && frozen(L, i, j, l)) continue;
-    u[idx] = point_update<T, DIM>(u, f, L, idx, i, j, l);
+    u[idx] = point_update<T, DIM, PER>(u, f, L, idx, i, j, l);
   }
 }
 
 // ---- r = f - A u (Sec. 2.2) over a range of cells; returns the thread's sum of (scale*r)^2.
-template <typename T, int DIM>
+template <typename T, int DIM, bool PER = false>
 __device__ __forceinline__ float residual_range(T* r, const T* u, const T* f, const LevelDesc<T>& L,
                                                 float nscale, int64_t t0, int64_t stride) {
   // nscale: power-of-two factor applied before squaring (keeps float squares in range)
@@ -44,7 +44,7 @@ __device__ __forceinline__ float residual_range(T* r, const T* u, const T* f, co
     const int i = (int)(idx & (L.nx - 1));
     const int j = (int)((idx >> L.lx) & (L.ny - 1));
     const int l = (int)(idx >> (L.lx + L.ly));
-    const T rv = (L.fax >= 0 && frozen(L, i, j, l)) ? T(0) : residual_point<T, DIM>(u, f, L, idx, i, j, l);
+    const T rv = (L.fax >= 0 && frozen(L, i, j, l)) ? T(0) : residual_point<T, DIM, PER>(u, f, L, idx, i, j, l);
     if (r) r[idx] = rv;
     const float rs = (float)rv * nscale;
     acc = fmaf(rs, rs, acc);
@@ -86,7 +86,7 @@ __device__ __forceinline__ void restrict_range(T* uc, T* uc0, T* fc, const T* u,
 }
 
 // ---- tau correction (Algorithm 1, coarse source term): fc <- fc + A_c uc, fc holding R(r).
-template <typename T, int DIM>
+template <typename T, int DIM, bool PER = false>
 __device__ __forceinline__ void tau_range(T* fc, const T* uc, const LevelDesc<T>& Lc, int64_t t0,
                                           int64_t stride) {
   const int64_t n = (int64_t)Lc.nx * Lc.ny * Lc.nz;
@@ -95,7 +95,7 @@ __device__ __forceinline__ void tau_range(T* fc, const T* uc, const LevelDesc<T>
     const int j = (int)((idx >> Lc.lx) & (Lc.ny - 1));
     const int l = (int)(idx >> (Lc.lx + Lc.ly));
     if (Lc.fax >= 0 && frozen(Lc, i, j, l)) continue;
-    fc[idx] = fc[idx] + apply_point<T, DIM>(uc, Lc, idx, i, j, l);
+    fc[idx] = fc[idx] + apply_point<T, DIM, PER>(uc, Lc, idx, i, j, l);
   }
 }
 
@@ -265,7 +265,10 @@ __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * block
 
 template <typename T, int DIM>
 __global__ void k_smooth_colour(T* u, const T* f, LevelDesc<T> L, int colour) {
-  smooth_colour_range<T, DIM>(u, f, L, colour, gtid(), gstride());
+  if (L.per)
+    smooth_colour_range<T, DIM, true>(u, f, L, colour, gtid(), gstride());
+  else
+    smooth_colour_range<T, DIM, false>(u, f, L, colour, gtid(), gstride());
 }
 
 // One colour phase with a thread per group of 4 consecutive cells of a row (nx a multiple of 4,
@@ -363,7 +366,8 @@ __global__ void k_smooth_colour4(T* u, const T* f, LevelDesc<T> L, int colour) {
 // r (nullable) = f - A u; per-block partial of sum (s r)^2 into partials[blockIdx.x], s = *nsp (or 1).
 template <typename T, int DIM>
 __global__ void k_residual(T* r, const T* u, const T* f, LevelDesc<T> L, const float* nsp, double* partials) {
-  const float acc = residual_range<T, DIM>(r, u, f, L, nsp ? *nsp : 1.f, gtid(), gstride());
+  const float acc = L.per ? residual_range<T, DIM, true>(r, u, f, L, nsp ? *nsp : 1.f, gtid(), gstride())
+                          : residual_range<T, DIM, false>(r, u, f, L, nsp ? *nsp : 1.f, gtid(), gstride());
   const double s = block_sum((double)acc);
   if (threadIdx.x == 0 && partials) partials[blockIdx.x] = s;
 }
@@ -391,7 +395,10 @@ __global__ void k_restrict(T* uc, T* uc0, T* fc, const T* u, const T* r, int nxf
 
 template <typename T, int DIM>
 __global__ void k_tau(T* fc, const T* uc, LevelDesc<T> Lc) {
-  tau_range<T, DIM>(fc, uc, Lc, gtid(), gstride());
+  if (Lc.per)
+    tau_range<T, DIM, true>(fc, uc, Lc, gtid(), gstride());
+  else
+    tau_range<T, DIM, false>(fc, uc, Lc, gtid(), gstride());
 }
 
 template <typename T, int DIM>
@@ -495,7 +502,9 @@ __global__ void k_ir_residual(float* r32, const double* u, const double* b, Leve
           done = true;
         }
       }
-      if (!done) r = residual_point<double, DIM>(u, b, L, idx, i, j, l);
+      if (!done)
+        r = L.per ? residual_point<double, DIM, true>(u, b, L, idx, i, j, l)
+                  : residual_point<double, DIM, false>(u, b, L, idx, i, j, l);
       rv = f64_to_f32_rn_bits(r);
     }
     r32[idx] = rv;
@@ -593,13 +602,13 @@ struct CoarseArgs {
 // 3D) for a forward sweep; a symmetric ordering runs every second sweep backward.
 __host__ __device__ __forceinline__ int first_colour(int ordering, int s) { return (ordering == 1 && (s & 1)) ? 0 : 1; }
 
-template <typename T, int DIM>
+template <typename T, int DIM, bool PER>
 __device__ void coarse_smooth(T* u, const T* f, const LevelDesc<T>& L, int sweeps, int ordering) {
   for (int s = 0; s < sweeps; ++s) {
     const int c0 = first_colour(ordering, s);
-    smooth_colour_range<T, DIM>(u, f, L, c0, threadIdx.x, blockDim.x);
+    smooth_colour_range<T, DIM, PER>(u, f, L, c0, threadIdx.x, blockDim.x);
     __syncthreads();
-    smooth_colour_range<T, DIM>(u, f, L, 1 - c0, threadIdx.x, blockDim.x);
+    smooth_colour_range<T, DIM, PER>(u, f, L, 1 - c0, threadIdx.x, blockDim.x);
     __syncthreads();
   }
 }
@@ -616,7 +625,7 @@ struct SmemLayout {
   int64_t total;                                                      // elements
 };
 
-template <typename T, int DIM>
+template <typename T, int DIM, bool PER = false>
 __device__ __forceinline__ void restrict_resid_range(T* uc, T* uc0, T* fc, const T* u, const T* f,
                                                      const LevelDesc<T>& L, int64_t t0, int64_t stride) {
   const int nxf = L.nx, nyf = L.ny, nzf = L.nz;
@@ -638,7 +647,7 @@ __device__ __forceinline__ void restrict_resid_range(T* uc, T* uc0, T* fc, const
     for (int k = 0; k < (DIM == 3 ? 8 : 4); ++k) {
       const int di = k & 1, dj = (k >> 1) & 1, dl = (k >> 2) & 1;
       const int64_t idx = base + di + dj * sy + dl * sz;
-      r[k] = residual_point<T, DIM>(u, f, L, idx, i0 + di, j0 + dj, l0 + dl);
+      r[k] = residual_point<T, DIM, PER>(u, f, L, idx, i0 + di, j0 + dj, l0 + dl);
     }
     // same association as avg_children: (c00 + c01) + (c10 + c11) [+ the upper z layer]
     T sr = (r[0] + r[1]) + (r[2] + r[3]);
@@ -681,27 +690,20 @@ __device__ __forceinline__ void restrict_resid_face_range(T* uc, T* uc0, T* fc, 
 // followed by k_restrict / k_restrict_face, so the results are identical.
 template <typename T, int DIM, int FAX>
 __global__ void k_restrict_resid(T* uc, T* uc0, T* fc, const T* u, const T* f, LevelDesc<T> L) {
-  if constexpr (FAX < 0)
-    restrict_resid_range<T, DIM>(uc, uc0, fc, u, f, L, gtid(), gstride());
-  else
+  if constexpr (FAX < 0) {
+    if (L.per)
+      restrict_resid_range<T, DIM, true>(uc, uc0, fc, u, f, L, gtid(), gstride());
+    else
+      restrict_resid_range<T, DIM, false>(uc, uc0, fc, u, f, L, gtid(), gstride());
+  } else
     restrict_resid_face_range<T, DIM, FAX>(uc, uc0, fc, u, f, L, gtid(), gstride());
 }
 
-// FAX = -1: cell-centred levels; 0..2: face grids normal to that index axis.
-template <typename T, int DIM, int FAX>
-__global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayout S, T* utop, const T* ftop) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
+// The single-CTA V-cycle's work once its descriptors are in shared memory (sdesc, indexed by level).
+template <typename T, int DIM, int FAX, bool PER>
+__device__ __forceinline__ void coarse_body(const CoarseArgs<T>& A, const SmemLayout& S, T* utop, const T* ftop, T* sm,
+                                            const LevelDesc<T>* sdesc) {
   const int last = A.nlev - 1;
-  // level descriptors of levels l0..last, copied after the field arrays (every stencil reads them)
-  LevelDesc<T>* sdesc = reinterpret_cast<LevelDesc<T>*>(smem_raw + S.total * sizeof(T)) - A.l0;
-  {
-    const int words = (int)((A.nlev - A.l0) * sizeof(LevelDesc<T>) / sizeof(int));
-    const int* src = reinterpret_cast<const int*>(A.desc + A.l0);
-    int* dst = reinterpret_cast<int*>(sdesc + A.l0);
-    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
-  }
-  __syncthreads();
   {
     const LevelDesc<T>& L = sdesc[A.l0];
     const int64_t n = (int64_t)L.nx * L.ny * L.nz;
@@ -715,15 +717,15 @@ __global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayou
     const LevelDesc<T>& L = sdesc[l];
     T* u = sm + S.off_u[l];
     const T* f = sm + S.off_f[l];
-    coarse_smooth<T, DIM>(u, f, L, A.nu1, A.ordering);
+    coarse_smooth<T, DIM, PER>(u, f, L, A.nu1, A.ordering);
     if constexpr (FAX < 0)
-      restrict_resid_range<T, DIM>(sm + S.off_u[l + 1], sm + S.off_u0[l + 1], sm + S.off_f[l + 1], u, f, L,
+      restrict_resid_range<T, DIM, PER>(sm + S.off_u[l + 1], sm + S.off_u0[l + 1], sm + S.off_f[l + 1], u, f, L,
                                    threadIdx.x, blockDim.x);
     else
       restrict_resid_face_range<T, DIM, FAX>(sm + S.off_u[l + 1], sm + S.off_u0[l + 1], sm + S.off_f[l + 1], u, f,
                                              L, threadIdx.x, blockDim.x);
     __syncthreads();
-    tau_range<T, DIM>(sm + S.off_f[l + 1], sm + S.off_u[l + 1], sdesc[l + 1], threadIdx.x, blockDim.x);
+    tau_range<T, DIM, PER>(sm + S.off_f[l + 1], sm + S.off_u[l + 1], sdesc[l + 1], threadIdx.x, blockDim.x);
     __syncthreads();
   }
   {
@@ -740,7 +742,7 @@ __global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayou
       }
       __syncthreads();
     } else {
-      coarse_smooth<T, DIM>(u, f, L, A.nuc, A.ordering);
+      coarse_smooth<T, DIM, PER>(u, f, L, A.nuc, A.ordering);
     }
   }
   for (int l = last - 1; l >= A.l0; --l) {
@@ -753,13 +755,36 @@ __global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayou
       prolong_face_range<T, DIM, FAX>(u, sm + S.off_u[l + 1], sm + S.off_u0[l + 1], L.nx, L.ny, L.nz, threadIdx.x,
                                       blockDim.x);
     __syncthreads();
-    coarse_smooth<T, DIM>(u, f, L, A.nu2, A.ordering);
+    coarse_smooth<T, DIM, PER>(u, f, L, A.nu2, A.ordering);
   }
   {
     const LevelDesc<T>& L = sdesc[A.l0];
     const int64_t n = (int64_t)L.nx * L.ny * L.nz;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) utop[i] = sm[S.off_u[A.l0] + i];
   }
+}
+
+// FAX = -1: cell-centred levels; 0..2: face grids normal to that index axis.
+template <typename T, int DIM, int FAX>
+__global__ void __launch_bounds__(1024) k_coarse_smem(CoarseArgs<T> A, SmemLayout S, T* utop, const T* ftop) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  // level descriptors of levels l0..last, copied after the field arrays (every stencil reads them)
+  LevelDesc<T>* sdesc = reinterpret_cast<LevelDesc<T>*>(smem_raw + S.total * sizeof(T)) - A.l0;
+  {
+    const int words = (int)((A.nlev - A.l0) * sizeof(LevelDesc<T>) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(A.desc + A.l0);
+    int* dst = reinterpret_cast<int*>(sdesc + A.l0);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+  }
+  __syncthreads();
+  if constexpr (FAX < 0) {
+    if (sdesc[A.l0].per) {  // every level of a hierarchy has the same periodic axes
+      coarse_body<T, DIM, FAX, true>(A, S, utop, ftop, sm, sdesc);
+      return;
+    }
+  }
+  coarse_body<T, DIM, FAX, false>(A, S, utop, ftop, sm, sdesc);
 }
 
 // ------------------------------------------------------------------------------------------------

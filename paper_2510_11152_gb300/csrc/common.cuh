@@ -96,13 +96,6 @@ __device__ __forceinline__ T nbsum_t(const T* __restrict__ u, int64_t idx, int i
   }
 }
 
-template <typename T, int DIM>
-__device__ __forceinline__ T nbsum(const T* __restrict__ u, int64_t idx, int i, int j, int l, int nx, int ny, int nz,
-                                   int per) {
-  return per ? nbsum_t<T, DIM, true>(u, idx, i, j, l, nx, ny, nz, per)
-             : nbsum_t<T, DIM, false>(u, idx, i, j, l, nx, ny, nz, 0);
-}
-
 // Weighted neighbour sum sum_f w_f u_nb (per-cell kappa).
 template <typename T, int DIM>
 __device__ __forceinline__ T nbsum_w(const T* __restrict__ u, const LevelDesc<T>& L, int64_t idx, int i,
@@ -120,8 +113,9 @@ __device__ __forceinline__ T nbsum_w(const T* __restrict__ u, const LevelDesc<T>
   return acc;
 }
 
-// Gauss-Seidel point update of cell (i, j, l): the new value from the current neighbours.
-template <typename T, int DIM>
+// Gauss-Seidel point update of cell (i, j, l): the new value from the current neighbours. PER: the
+// level may have periodic axes (the kernels choose the instantiation once from the descriptor).
+template <typename T, int DIM, bool PER = false>
 __device__ __forceinline__ T point_update(const T* __restrict__ u, const T* __restrict__ f,
                                           const LevelDesc<T>& L, int64_t idx, int i, int j, int l) {
   if (L.varkappa) {
@@ -129,12 +123,12 @@ __device__ __forceinline__ T point_update(const T* __restrict__ u, const T* __re
     return fma(L.h2, f[idx], nw) * L.rD[idx];
   }
   const int cls = bclass<DIM>(i, j, l, L.nx, L.ny, L.nz);
-  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz, L.per);
+  T nb = nbsum_t<T, DIM, PER>(u, idx, i, j, l, L.nx, L.ny, L.nz, L.per);
   return fma(L.a[cls], nb, L.b[cls] * f[idx]);
 }
 
 // (A u) at cell (i, j, l).
-template <typename T, int DIM>
+template <typename T, int DIM, bool PER = false>
 __device__ __forceinline__ T apply_point(const T* __restrict__ u, const LevelDesc<T>& L, int64_t idx, int i,
                                          int j, int l) {
   if (L.varkappa) {
@@ -142,12 +136,12 @@ __device__ __forceinline__ T apply_point(const T* __restrict__ u, const LevelDes
     return fma(L.Dh[idx], u[idx], -L.ih2 * nw);
   }
   const int cls = bclass<DIM>(i, j, l, L.nx, L.ny, L.nz);
-  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz, L.per);
+  T nb = nbsum_t<T, DIM, PER>(u, idx, i, j, l, L.nx, L.ny, L.nz, L.per);
   return fma(L.d[cls], u[idx], -L.c * nb);
 }
 
 // Residual f - A u at cell (i, j, l).
-template <typename T, int DIM>
+template <typename T, int DIM, bool PER = false>
 __device__ __forceinline__ T residual_point(const T* __restrict__ u, const T* __restrict__ f,
                                             const LevelDesc<T>& L, int64_t idx, int i, int j, int l) {
   if (L.varkappa) {
@@ -155,7 +149,7 @@ __device__ __forceinline__ T residual_point(const T* __restrict__ u, const T* __
     return fma(L.ih2, nw, fma(-L.Dh[idx], u[idx], f[idx]));
   }
   const int cls = bclass<DIM>(i, j, l, L.nx, L.ny, L.nz);
-  T nb = nbsum<T, DIM>(u, idx, i, j, l, L.nx, L.ny, L.nz, L.per);
+  T nb = nbsum_t<T, DIM, PER>(u, idx, i, j, l, L.nx, L.ny, L.nz, L.per);
   return fma(L.c, nb, fma(-L.d[cls], u[idx], f[idx]));
 }
 

@@ -70,25 +70,40 @@ def test_profiler_reports_fused_kernels(cuda_lib):
     assert sm0["launches"] == info.cycles and sm0["ms"] > 0
 
 
+def _fused3d_vcycles(fas, shape, bc, nu, path, cycles=3):
+    h = 1.0 / shape[-1]
+    u0 = random_field(shape, 321)
+    f = noisy_cos_mode(shape, 322)
+    ctx = fas.fas_create(fas.make_params(shape, h, alpha=1.0, beta=2e-3, bc=bc, coarsest=4, precision=1,
+                                         path=path, nu1=nu, nu2=nu))
+    u = _t(u0)
+    ft = _t(f)
+    for _ in range(cycles):
+        fas.fas_vcycle(ctx, u, ft)
+    fas.fas_destroy(ctx)
+    return u.cpu().numpy()
+
+
+@pytest.mark.parametrize("bc", [(N_,) * 6, (D_, N_, N_, D_, N_, D_)])
+@pytest.mark.parametrize("nu", [2, 3])
+def test_fused_3d_sweep_full_size_level(cuda_lib, bc, nu):
+    """At a size the fused 3D sweep is used for (256 x 512 x 512, level 0): V-cycles equal the
+    per-operation path's bit for bit."""
+    fas = cuda_lib
+    shape = (256, 512, 512)
+    a = _fused3d_vcycles(fas, shape, bc, nu, 0, cycles=2)
+    b = _fused3d_vcycles(fas, shape, bc, nu, 1, cycles=2)
+    np.testing.assert_array_equal(a, b)
+
+
 @pytest.mark.parametrize("shape", [(16, 32, 128), (32, 64, 256), (8, 16, 128), (64, 128, 256), (32, 16, 512)])
 @pytest.mark.parametrize("bc", [(N_,) * 6, (D_,) * 6, (D_, N_, N_, D_, N_, D_)])
 @pytest.mark.parametrize("nu", [1, 2, 3])
 def test_fused_3d_sweep_equals_per_operation(cuda_lib, shape, bc, nu):
     """The sweep-fused 3D float32 smoothing (both colour phases in one pass, pairs of sweeps ping-pong
-    between two buffers) gives the per-operation colour launches' mixed-precision iterates bit for
-    bit: strips of 128 columns, row groups that do not divide ny, short plane segments, every boundary
-    kind, an odd sweep count (its last sweep runs per colour phase)."""
+    between two buffers; path 2 uses it on levels below the size where it pays) gives the
+    per-operation colour launches' mixed-precision iterates bit for bit: strips of 128 columns, row
+    groups that do not divide ny, short plane segments, every boundary kind, an odd sweep count (its
+    last sweep runs per colour phase)."""
     fas = cuda_lib
-    h = 1.0 / shape[-1]
-    u0 = random_field(shape, 321)
-    f = noisy_cos_mode(shape, 322)
-    outs = []
-    for path in (0, 1):
-        ctx = fas.fas_create(fas.make_params(shape, h, alpha=1.0, beta=2e-3, bc=bc, coarsest=4, precision=1,
-                                             path=path, nu1=nu, nu2=nu))
-        u = _t(u0)
-        for _ in range(3):
-            fas.fas_vcycle(ctx, u, _t(f))
-        outs.append(u.cpu().numpy())
-        fas.fas_destroy(ctx)
-    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(_fused3d_vcycles(fas, shape, bc, nu, 2), _fused3d_vcycles(fas, shape, bc, nu, 1))

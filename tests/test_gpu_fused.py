@@ -27,7 +27,7 @@ def test_fused_equals_per_operation(cuda_lib, shape, bc, nu, inner):
     u0 = random_field(shape, 301)
     f = noisy_cos_mode(shape, 302)
     outs = []
-    for path in (0, 1):
+    for path in (0, 2, 1):  # default, fused on every level the kernels handle, per-operation
         ctx = fas.fas_create(fas.make_params(shape, h, alpha=1.0, beta=2e-3, bc=bc, coarsest=4, precision=1,
                                              path=path, nu1=nu, nu2=nu, inner_cycles=inner))
         u = _t(u0)
@@ -35,7 +35,8 @@ def test_fused_equals_per_operation(cuda_lib, shape, bc, nu, inner):
             fas.fas_vcycle(ctx, u, _t(f))
         outs.append(u.cpu().numpy())
         fas.fas_destroy(ctx)
-    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+    np.testing.assert_array_equal(outs[1], outs[2])
 
 
 @pytest.mark.parametrize("seg", [8, 16, 64, 256])
@@ -45,7 +46,7 @@ def test_fused_segment_sizes(cuda_lib, seg):
     u0 = random_field(shape, 311)
     f = random_field(shape, 312, -1, 1)
     outs = []
-    for path, sg in ((0, seg), (1, 0)):
+    for path, sg in ((2, seg), (1, 0)):
         ctx = fas.fas_create(fas.make_params(shape, 1.0 / 512, beta=1e-3, precision=1, path=path, seg_rows=sg))
         u = _t(u0)
         for _ in range(3):

@@ -473,3 +473,24 @@ def test_paper_second_order_convergence_table(cuda_lib):
     for row in range(1, len(errs)):
         for k in (0, 1):
             assert 3.6 < errs[row - 1][k] / errs[row][k] < 4.6, (row, k, errs)
+
+
+@pytest.mark.parametrize("shape,steps,order", [((512, 512), 2, 1), ((64, 64, 64), 2, 1), ((128, 128, 128), 1, 1),
+                                               ((64, 64, 64), 2, 2)])
+def test_projection_steps_larger_grids_match_oracle(cuda_lib, shape, steps, order):
+    """Projection steps on larger grids than the other parity tests (up to 128^3, where the oracle
+    still runs a step in seconds): every field within 1e-12 relative max-norm of the oracle's (the
+    pressure increment 1e-11), equal cycle counts, float64 solves."""
+    fas = cuda_lib
+    dim = len(shape)
+    ns, prm, h = _ns_pair(fas, shape, 0, dt=2e-3, order=order)
+    ref = ns_state(shape, 591) if order == 1 else _state2(shape, 592)
+    gpu = {k: _t(v) for k, v in ref.items()}
+    step_fn = st.projection_step if order == 1 else st.projection_step2
+    for step in range(steps):
+        infos, _ = fas.ns_projection_step(ns, gpu)
+        infos_ref, _, rhs_ref = step_fn(ref, shape, h, prm)
+        got = [infos[a] for a in range(dim)] + [infos[3]]
+        assert [i.cycles for i in got] == [i.cycles for i in infos_ref], "step %d" % step
+        for k in _fields_dim(dim):
+            assert _rel(_n(gpu[k]), ref[k]) <= _bar(k), (step, k, _rel(_n(gpu[k]), ref[k]))

@@ -423,9 +423,24 @@ def _event_ms(stream, fn, warmup=1):
     return e0.elapsed_time(e1), out
 
 
+def tune_inner(stream, make, candidates=(1, 2, 3)):
+    """The float32 cycles per refinement step with the shortest time to solution, the way the headline
+    workload is tuned: make(inner) returns (run, cleanup); each candidate is run once untimed and once
+    timed with CUDA events. Returns (inner, {inner: ms})."""
+    times = {}
+    for inner in candidates:
+        run, cleanup = make(inner)
+        ms, _ = _event_ms(stream, run)
+        times[inner] = ms
+        cleanup()
+    best = min(times, key=times.get)
+    return best, times
+
+
 def secondary_workloads(dev, stream, ws=1, rank=0):
     """The other workloads of the method, each once after one warm-up run (float64 vs mixed where both
-    apply): 3D heat 512^3, the 256^3 lid-driven cavity projection steps, 96 batched Helmholtz solves in
+    apply; the mixed arm's float32 cycles per refinement step tuned by time to solution first, as for
+    the headline workload): 3D heat 512^3, the 256^3 lid-driven cavity projection steps, 96 batched Helmholtz solves in
     one graph launch, the 512^2 grain-growth step with 1189 order parameters (periodic solves), the
     1024^2 adjoint heat run. Inputs are the seeded recipes of workloads/. Under
     several ranks the batched problems are shared out (cell-balanced, no data exchange) and the other
@@ -447,17 +462,27 @@ def secondary_workloads(dev, stream, ws=1, rank=0):
     f = torch.from_numpy(w["fsrc"]).to(dev) if w.get("fsrc") is not None else None
     u = torch.empty_like(u0)
     res = {}
-    for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
-        ctx = fas.fas_create(fas.make_params(shape, h, alpha=1.0, beta=dt, coarsest=4, precision=prec), stream=stream)
+
+    def make_heat(prec, inner):
+        ctx = fas.fas_create(fas.make_params(shape, h, alpha=1.0, beta=dt, coarsest=4, precision=prec,
+                                             inner_cycles=inner), stream=stream)
 
         def run():
             u.copy_(u0)
             return fas.fas_heat_run(ctx, u, f, dt, nsteps)
+        return run, lambda: fas.fas_destroy(ctx)
+    inner3, tune3 = tune_inner(stream, lambda k: make_heat(fas.FAS_MIXED, k))
+    for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
+        inner = inner3 if prec == fas.FAS_MIXED else 1
+        run, done = make_heat(prec, inner)
         ms, infos = _event_ms(stream, run)
-        cyc = sum(i.cycles for i in infos)
+        cyc = sum(i.cycles for i in infos) * inner
         res[name] = {"ms_per_run": ms, "vcycles_per_run": cyc, "Mcells_vcycles_per_s": mc(cells, cyc, ms),
                      "converged_all": all(i.converged for i in infos), "u": u.clone()}
-        fas.fas_destroy(ctx)
+        if prec == fas.FAS_MIXED:
+            res[name]["inner_float32_cycles"] = inner
+            res[name]["ms_per_run_by_inner_cycles"] = {str(k): v for k, v in tune3.items()}
+        done()
     out["heat3d_512"] = {
         "workload": "heat3d-512^3-neumann-dt1e-4-10steps-tol1e-10-V(2,2)-coarsest4",
         "mixed": {k: v for k, v in res["mixed"].items() if k != "u"},
@@ -475,11 +500,12 @@ def secondary_workloads(dev, stream, ws=1, rank=0):
     zero = torch.zeros(shape, dtype=torch.float64, device=dev)
     for order in (1, 2):
       ns_res = {}
-      for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
+
+      def make_ns(prec, inner):
         sp = fas.fas_default_params()
-        sp.precision, sp.kmax, sp.coarsest = prec, 40, 4
+        sp.precision, sp.kmax, sp.coarsest, sp.inner_cycles = prec, 40, 4, inner
         pp = fas.fas_default_params()
-        pp.precision, pp.kmax, pp.coarsest, pp.coarse_exact = prec, 60, 4, 1
+        pp.precision, pp.kmax, pp.coarsest, pp.coarse_exact, pp.inner_cycles = prec, 60, 4, 1, inner
         ns = fas.ns_create(shape, w["h"], w["Re"], w["dt"], lid=w["lid"], order=order, solver=sp, pressure=pp,
                            stream=stream)
         flds = {k: zero.clone() for k in w["fields"]}
@@ -491,14 +517,25 @@ def secondary_workloads(dev, stream, ws=1, rank=0):
             for _ in range(nsteps):
                 infos, div = fas.ns_projection_step(ns, flds, want_div=False)
                 for k in range(4):
-                    tot[k] += infos[k].cycles
+                    tot[k] += infos[k].cycles * inner
             return tot
+        return ns, flds, run
+      def ns_candidate(k):
+        ns_k, _, run_k = make_ns(fas.FAS_MIXED, k)
+        return run_k, lambda: fas.ns_destroy(ns_k)
+      inner_ns, tune_ns = tune_inner(stream, ns_candidate)
+      for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
+        inner = inner_ns if prec == fas.FAS_MIXED else 1
+        ns, flds, run = make_ns(prec, inner)
         fas.ns_launch_count(ns, reset=True)
         ms, tot = _event_ms(stream, run)
         _, dmax = fas.ns_projection_step(ns, flds, want_div=True)
         ns_res[name] = {"ms_per_step": ms / nsteps, "vcycles_per_step_u_v_w_p": [c / nsteps for c in tot],
                         "Mcells_vcycles_per_s": mc(cells, sum(tot), ms), "div_max_after": dmax,
                         "U": (flds["U_old"] if order == 1 else flds["U_new"]).clone()}
+        if prec == fas.FAS_MIXED:
+            ns_res[name]["inner_float32_cycles"] = inner
+            ns_res[name]["ms_per_step_by_inner_cycles"] = {str(k): v / nsteps for k, v in tune_ns.items()}
         del flds
         fas.ns_destroy(ns)
       key = "ns_cavity_256" if order == 1 else "ns_cavity_256_order2"
@@ -572,24 +609,32 @@ def secondary_workloads(dev, stream, ws=1, rank=0):
     del w["etas"]
     gsteps = 3
     ggr = {}
-    for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
-        sp = fas.fas_default_params()
-        sp.precision, sp.kmax, sp.coarsest = prec, 40, 4
-        ctx = fas.gg_create(shape, w["h"], w["dt"], q, solver=sp, stream=stream)
-        eta = eta0.clone()
-        fas.gg_step(ctx, eta)  # warm-up: builds the batch graphs
-        eta.copy_(eta0)
+    eta = eta0.clone()
 
-        def run_g():
+    def make_gg(prec, inner):
+        sp = fas.fas_default_params()
+        sp.precision, sp.kmax, sp.coarsest, sp.inner_cycles = prec, 40, 4, inner
+        ctx = fas.gg_create(shape, w["h"], w["dt"], q, solver=sp, stream=stream)
+
+        def run_g():  # the first call also builds the batch graphs
+            eta.copy_(eta0)
             cyc = 0
             for _ in range(gsteps):
-                cyc += sum(i.cycles for i in fas.gg_step(ctx, eta))
+                cyc += sum(i.cycles for i in fas.gg_step(ctx, eta)) * inner
             return cyc
-        ms, cyc = _event_ms(stream, run_g, warmup=0)
+        return run_g, lambda: fas.gg_destroy(ctx)
+    inner_gg, tune_gg = tune_inner(stream, lambda k: make_gg(fas.FAS_MIXED, k))
+    for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
+        inner = inner_gg if prec == fas.FAS_MIXED else 1
+        run_g, done = make_gg(prec, inner)
+        ms, cyc = _event_ms(stream, run_g)
         ggr[name] = {"ms_per_step": ms / gsteps, "vcycles_per_step": cyc / gsteps,
                      "Mcells_vcycles_per_s": mc(cells, cyc, ms), "eta": eta.clone()}
-        fas.gg_destroy(ctx)
-        del eta
+        if prec == fas.FAS_MIXED:
+            ggr[name]["inner_float32_cycles"] = inner
+            ggr[name]["ms_per_step_by_inner_cycles"] = {str(k): v / gsteps for k, v in tune_gg.items()}
+        done()
+    del eta
     out["grain_growth_512"] = {
         "workload": "grain growth 512^2 periodic, q=1189 order parameters, h 2, dt 0.25, %d steps from "
                     "U(-0.001,0.001), linearly implicit step, tol 1e-10" % gsteps,
@@ -609,23 +654,30 @@ def secondary_workloads(dev, stream, ws=1, rank=0):
     fsrc = torch.from_numpy(w["fsrc"]).to(dev)
     tgt = torch.from_numpy(w["target"]).to(dev)
     adj = {}
-    for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
-        ctx = fas.fas_create(fas.make_params(shape, w["h"], alpha=1.0, beta=w["dt"], coarsest=4, precision=prec),
-                             stream=stream, kappa=kap)
-        uT = torch.empty_like(u0)
-        g = [torch.empty_like(u0) for _ in range(3)]
-        fwd = torch.empty_like(u0)
+    uT = torch.empty_like(u0)
+    g = [torch.empty_like(u0) for _ in range(3)]
+    fwd = torch.empty_like(u0)
+
+    def make_adj(prec, inner):
+        ctx = fas.fas_create(fas.make_params(shape, w["h"], alpha=1.0, beta=w["dt"], coarsest=4, precision=prec,
+                                             inner_cycles=inner), stream=stream, kappa=kap)
 
         def run_a():
             fwd.copy_(u0)
             fas.fas_heat_run(ctx, fwd, fsrc, w["dt"], w["nsteps"])
             dl = 2.0 * (fwd - tgt)
             fas.fas_heat_adjoint(ctx, u0, fsrc, w["dt"], w["nsteps"], dl, uT, g[0], g[1], g[2], 10)
+        return run_a, lambda: fas.fas_destroy(ctx)
+    inner_adj, tune_adj = tune_inner(stream, lambda k: make_adj(fas.FAS_MIXED, k))
+    for prec, name in ((fas.FAS_MIXED, "mixed"), (fas.FAS_FP64, "fp64")):
+        run_a, done = make_adj(prec, inner_adj if prec == fas.FAS_MIXED else 1)
         ms, _ = _event_ms(stream, run_a)
         adj[name] = {"ms_forward_plus_adjoint": ms, "g_kappa": g[2].clone()}
-        fas.fas_destroy(ctx)
+        done()
     out["adjoint_1024"] = {"workload": "adjoint heat 1024^2, varying kappa, 50 steps, checkpoints every 10",
-                           "mixed": {"ms_forward_plus_adjoint": adj["mixed"]["ms_forward_plus_adjoint"]},
+                           "mixed": {"ms_forward_plus_adjoint": adj["mixed"]["ms_forward_plus_adjoint"],
+                                     "inner_float32_cycles": inner_adj,
+                                     "ms_by_inner_cycles": {str(k): v for k, v in tune_adj.items()}},
                            "fp64": {"ms_forward_plus_adjoint": adj["fp64"]["ms_forward_plus_adjoint"]},
                            "mixed_vs_fp64_rel_maxdiff_g_kappa": float(
                                (adj["mixed"]["g_kappa"] - adj["fp64"]["g_kappa"]).abs().max().item()

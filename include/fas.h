@@ -312,12 +312,16 @@ fas_status fas_selftest_conversions(long long count, unsigned long long seed, lo
  * waits for it; FAS_ECUDA if a CUDA call fails. */
 fas_status fas_probe_fp64_rate(double* tflops);
 
-/* Test hook of the bounded device waits (no counterpart in the paper). The 3D refinement residual
- * streams its planes into shared memory with TMA tile copies and waits for each on an mbarrier; a
- * wait gives up after limit_ns nanoseconds (default 1e9), the kernel stops its work and sets an error
- * word, and the call that launched it returns FAS_ETIMEOUT (the context stays usable). limit_ns sets
- * that deadline for later launches; withhold_next != 0 makes the next launch of that kernel withhold
- * one copy (the first of block 0), so that its waits run out. Process-wide; FAS_EINVAL if limit_ns <= 0. */
+/* Test hook of the bounded device waits (no counterpart in the paper). The 3D refinement residual and
+ * the sweep-fused 3D smoother stream their planes into shared memory with TMA tile copies and wait for
+ * each on an mbarrier; a wait gives up after limit_ns nanoseconds (default 1e9), the kernel stops its
+ * work and sets an error word, and the call that launched it returns FAS_ETIMEOUT (the context stays
+ * usable). limit_ns sets that deadline for later launches; withhold_next = 1 makes the next launch of
+ * the refinement residual, 2 the next launch of the fused sweep, withhold one copy (the first of
+ * block 0), so that its waits run out; 0 withholds nothing. The request applies to the next launch
+ * enqueued, and a launch captured into a solve's CUDA graph keeps it on every replay, so the hook is
+ * meant for contexts with use_graph 0 or for calls that are not captured (fas_residual_ir).
+ * Process-wide; FAS_EINVAL if limit_ns <= 0 or withhold_next is not 0, 1 or 2. */
 fas_status fas_debug_bounded_wait(long long limit_ns, int withhold_next);
 
 /* Thread-local message describing the last error on this thread ("" if none). */

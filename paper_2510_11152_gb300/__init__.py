@@ -304,10 +304,11 @@ def fas_probe_fp64_rate() -> float:
     return out.value
 
 
-def fas_debug_bounded_wait(limit_ns: int, withhold_next: bool = False) -> None:
+def fas_debug_bounded_wait(limit_ns: int, withhold_next: int = 0) -> None:
     """Deadline of the kernels' bounded waits, and the test hook that withholds one copy of the next
-    launch of the 3D refinement residual (its waits then run out: FAS_ETIMEOUT)."""
-    _check(load().fas_debug_bounded_wait(int(limit_ns), 1 if withhold_next else 0), "fas_debug_bounded_wait")
+    launch of the 3D refinement residual (withhold_next 1) or of the fused 3D sweep (2); its waits then
+    run out and the call reports FAS_ETIMEOUT."""
+    _check(load().fas_debug_bounded_wait(int(limit_ns), int(withhold_next)), "fas_debug_bounded_wait")
 
 
 def fas_smooth(ctx: _Ctx, level: int, u, f, sweeps: int) -> None:

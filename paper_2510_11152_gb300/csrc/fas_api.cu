@@ -32,7 +32,14 @@ thread_local std::string g_last_error;
 // Bounded waits of the tile copies (the 3D refinement residual): the deadline of one wait, and the
 // test hook that withholds one copy of the next launch (fas_debug_bounded_wait).
 std::atomic<unsigned long long> g_wait_limit_ns{kTmaWaitNs};
-std::atomic<int> g_withhold_copy{0};
+std::atomic<int> g_withhold_copy{0};  // 0 none, 1 the next refinement residual, 2 the next fused sweep
+
+// 1 (and the request cleared) when the test hook asks to withhold a copy of the next launch of kernel
+// `which` (1 refinement residual, 2 fused 3D sweep).
+int take_withhold(int which) {
+  int expect = which;
+  return g_withhold_copy.compare_exchange_strong(expect, 0) ? 1 : 0;
+}
 
 fas_status fail(fas_status s, const std::string& msg) {
   g_last_error = msg;
@@ -490,13 +497,13 @@ void launch_smooth(fas_ctx* c, const LevelDesc<T>& L, int level, T* u, const T* 
         {
           Prof pr(c, FAS_K_SMOOTH, level, (double)(2 * half));
           e = launch_sweep3d(scratch, u, f, L, first_colour(c->p.ordering, s0), c->sm_count, c->ir_ticket + 2,
-                             g_wait_limit_ns.load(), c->stream);
+                             g_wait_limit_ns.load(), take_withhold(2), c->stream);
         }
         if (e != cudaSuccess) break;  // nothing was launched: the colour launches below do the sweeps
         {
           Prof pr(c, FAS_K_SMOOTH, level, (double)(2 * half));
           e = launch_sweep3d(u, scratch, f, L, first_colour(c->p.ordering, s0 + 1), c->sm_count, c->ir_ticket + 2,
-                             g_wait_limit_ns.load(), c->stream);
+                             g_wait_limit_ns.load(), take_withhold(2), c->stream);
         }
         if (e != cudaSuccess) {  // one sweep done, into scratch: bring it back
           cudaMemcpyAsync(u, scratch, (size_t)(2 * half) * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
@@ -685,7 +692,7 @@ int launch_ir_residual(fas_ctx* c, float* r32, const double* u, const double* b,
   Prof pr(c, FAS_K_IR, 0, (double)n);
   if (ir_strip_supported(L) &&
       launch_ir_strip(r32, u, b, L, nsp, c->partials, c->ir_ticket, c->sm_count, c->max_blocks, &g, c->stream,
-                      Ir3Wait{g_wait_limit_ns.load(), g_withhold_copy.exchange(0)}) == cudaSuccess)
+                      Ir3Wait{g_wait_limit_ns.load(), take_withhold(1)}) == cudaSuccess)
     ;  // the strip kernels took the level
   else if (c->p.dim == 2)
     k_ir_residual<2><<<g, kBlock, 0, c->stream>>>(r32, u, b, L, nsp, c->partials);
@@ -1893,8 +1900,9 @@ fas_status fas_prof_read(fas_ctx* c, fas_prof_record* out, int cap, int* count) 
 
 fas_status fas_debug_bounded_wait(long long limit_ns, int withhold_next) {
   if (limit_ns <= 0) return fail(FAS_EINVAL, "fas_debug_bounded_wait: limit_ns must be positive");
+  if (withhold_next < 0 || withhold_next > 2) return fail(FAS_EINVAL, "fas_debug_bounded_wait: withhold_next is 0, 1 or 2");
   g_wait_limit_ns = (unsigned long long)limit_ns;
-  g_withhold_copy = withhold_next ? 1 : 0;
+  g_withhold_copy = withhold_next;
   return FAS_OK;
 }
 

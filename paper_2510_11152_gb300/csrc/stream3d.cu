@@ -104,7 +104,7 @@ __device__ __forceinline__ float phase1_halo(const float* row, const float* rs, 
 
 __global__ void __launch_bounds__(kS3Threads, 2)
     k_sweep3d(float* __restrict__ uout, const __grid_constant__ CUtensorMap tu, const __grid_constant__ CUtensorMap tf,
-              LevelDesc<float> L, int c1, int zseg, unsigned* err, unsigned long long wait_ns) {
+              LevelDesc<float> L, int c1, int zseg, unsigned* err, unsigned long long wait_ns, int withhold) {
   extern __shared__ __align__(128) unsigned char smem_s3[];
   float* su = reinterpret_cast<float*>(smem_s3 + ((128u - (smem_u32(smem_s3) & 127u)) & 127u));
   float* sf = su + kUDepth * kUSlot;
@@ -155,10 +155,12 @@ __global__ void __launch_bounds__(kS3Threads, 2)
       tma_load_3d(sf + mod(z, kFDepth) * kFSlot, &tf, xs - kS3Off, y0 - 1, z, bar + k);
       pend |= 1u << k;
     };
+    // the test hook withholds one copy (block 0, first task): its waits must run out
+    const bool hold = withhold && blockIdx.x == 0 && task == (int)blockIdx.x;
     if (tid == 0) {
       fence_async_smem();  // the previous task's reads of the slots come before the new copies
       for (int z = z0 - 2; z <= z0; ++z)
-        if (u_ok(z)) issue_u(z);
+        if (u_ok(z) && !(hold && z == z0)) issue_u(z);
       if (f_ok(z0 - 1)) issue_f(z0 - 1);
     }
     bool ok = true;
@@ -227,7 +229,7 @@ cudaError_t sweep3d_prepare() {
 }
 
 cudaError_t launch_sweep3d(float* uout, const float* uin, const float* f, const LevelDesc<float>& L, int c1,
-                           int sm_count, unsigned* err, unsigned long long wait_ns, cudaStream_t stream) {
+                           int sm_count, unsigned* err, unsigned long long wait_ns, int withhold, cudaStream_t stream) {
   // plane segments of 32..256 (four extra planes each) sized for about four tasks per block
   const int64_t cols = (int64_t)(L.nx / kS3Cols) * ((L.ny + kS3Rows - 1) / kS3Rows);
   const int64_t wave = (int64_t)sm_count * 2;
@@ -239,7 +241,7 @@ cudaError_t launch_sweep3d(float* uout, const float* uin, const float* f, const 
   cudaError_t e = tensor_map_3d(&tu, uin, sizeof(float), L.nx, L.ny, L.nz, kS3Pitch, kUTileRows, 1);
   if (e == cudaSuccess) e = tensor_map_3d(&tf, f, sizeof(float), L.nx, L.ny, L.nz, kS3Pitch, kFTileRows, 1);
   if (e != cudaSuccess) return e;
-  k_sweep3d<<<blocks, kS3Threads, kS3Smem, stream>>>(uout, tu, tf, L, c1, zseg, err, wait_ns);
+  k_sweep3d<<<blocks, kS3Threads, kS3Smem, stream>>>(uout, tu, tf, L, c1, zseg, err, wait_ns, withhold);
   return cudaGetLastError();
 }
 

@@ -192,14 +192,38 @@ def test_bounded_wait_runs_out_and_context_stays_usable(cuda_lib):
     r32 = torch.empty(u.size, dtype=torch.float32, device="cuda")
     n0 = fas.fas_residual_ir(ctx, ut, ft, r32)
     r_ref = r32.clone()
-    fas.fas_debug_bounded_wait(20_000_000, withhold_next=True)  # 20 ms
+    fas.fas_debug_bounded_wait(20_000_000, withhold_next=1)  # 20 ms
     try:
         with pytest.raises(fas.FasError) as e:
             fas.fas_residual_ir(ctx, ut, ft, r32)
         assert e.value.status == fas.FAS_ETIMEOUT
     finally:
-        fas.fas_debug_bounded_wait(1_000_000_000, withhold_next=False)
+        fas.fas_debug_bounded_wait(1_000_000_000, withhold_next=0)
     n1 = fas.fas_residual_ir(ctx, ut, ft, r32)
     assert torch.equal(r32, r_ref) and abs(n1 - n0) <= 1e-9 * n0
     x = _t(np.zeros(shape))
     assert fas.fas_solve(ctx, x, ft).converged
+
+
+def test_bounded_wait_of_the_fused_sweep(cuda_lib):
+    """The same for the sweep-fused 3D smoother (forced on a small level with path 2): a withheld tile
+    copy makes the V-cycle return FAS_ETIMEOUT after the deadline; the next V-cycle on the same context
+    from the same start gives the result of an undisturbed context bit for bit."""
+    fas = cuda_lib
+    shape = (32, 64, 128)
+    params = fas.make_params(shape, 1.0 / 128, alpha=1.0, beta=2e-3, precision=fas.FAS_MIXED, path=2, use_graph=0)
+    u0 = random_field(shape, 631)
+    f = _t(random_field(shape, 632, -1, 1))
+    ref = _t(u0)
+    fas.fas_vcycle(fas.fas_create(params), ref, f)
+    ctx = fas.fas_create(params)
+    fas.fas_debug_bounded_wait(20_000_000, withhold_next=2)
+    try:
+        with pytest.raises(fas.FasError) as e:
+            fas.fas_vcycle(ctx, _t(u0), f)
+        assert e.value.status == fas.FAS_ETIMEOUT
+    finally:
+        fas.fas_debug_bounded_wait(1_000_000_000, withhold_next=0)
+    u = _t(u0)
+    fas.fas_vcycle(ctx, u, f)
+    np.testing.assert_array_equal(u.cpu().numpy(), ref.cpu().numpy())

@@ -154,20 +154,22 @@ def measured_peaks():
 # algorithmic work per cell of each kernel family (bytes or float64 operations)
 # ---------------------------------------------------------------------------------------------
 
-def kernel_work(family, level, inner_first_zero=True):
+def kernel_work(family, level, inner=1):
     """(bound, per-cell work, unit) of a kernel family on a level of the mixed-precision solver.
-    Bytes that must cross HBM once (b = 4 for float32 fields, 8 for float64)."""
+    Bytes that must cross HBM once (b = 4 for float32 fields, 8 for float64). inner = float32 cycles
+    per refinement step: the first level-0 pre-smoothing of a step starts from zero (no u read), the
+    others read u, so the family's per-launch bytes are their average."""
     b = 4.0
     if family == "smooth":  # fused pre-smoothing: f (+u, +R(r)) in, u and R(u), R(r) out
         if level == 0:
-            return "hbm", (2.5 if inner_first_zero else 3.5) * b, "B"
+            return "hbm", (2.5 + 3.5 * (inner - 1)) / inner * b, "B"
         return "hbm", 4.5 * b, "B"
     if family == "prolong":  # fused post-smoothing: u, f, u_c in; u out
         return "hbm", 3.25 * b, "B"
     if family == "ir":  # r32 = (float)(b - A u): u, b in (float64), r32 out; the exact-difference kernel
         return "hbm", 8.0 + 8.0 + b, "B"  # also has a float64 floor of 2 DFMA per cell (fp64_work)
     if family == "update":  # fused post-smoothing + u += e: u, f, u_c in (float32), float64 u in/out
-        return "hbm", 3.0 * b + 1.0 + 16.0, "B"
+        return "hbm", 2.25 * b + 16.0, "B"
     return None, None, None
 
 
@@ -297,7 +299,7 @@ def run_ours(args, ws, rank, local):
     def roofline_of(r):
         """Both floors of a kernel family: HBM (algorithmic bytes) and, where it executes float64
         arithmetic, the FP64 pipe (algorithmic FLOPs); the binding one (the larger time floor) leads."""
-        bound, work, unit = kernel_work(r["family"], r["level"])
+        bound, work, unit = kernel_work(r["family"], r["level"], inner)
         if bound is None:
             return None
         per_launch_units = r["units"] / r["launches"]

@@ -9,7 +9,10 @@
 //     -> residual r = f - A u at the next row -> on odd rows, the 2x2 averages R(u), R(r) (Appendix C)
 //   post-smoothing kernel (coarse-grid correction and post-smoothing)
 //     load row y -> on odd rows u += uc - R(u) for the row pair (Appendix C prolongation of the
-//     correction, R(u) recomputed from the unchanged fine values) -> colour phases -> store.
+//     correction, R(u) recomputed from the unchanged fine values) -> colour phases -> store; the
+//     coarse values of a row pair travel in the row ring with the pair's second row. In the last
+//     float32 cycle of a refinement step the store is u64 += e instead: the row is staged in shared
+//     memory as float64 and added to u64 by a bulk reduction in the L2.
 //
 // A colour phase updates the cells of one X-MCGS colour (Sec. 2.3; colour 1 = cells whose 1-based
 // i+j is odd, the paper's sets 1 and 2) from their four neighbours. A row's cells of one colour only
@@ -30,6 +33,7 @@
 #include "common.cuh"
 #include "cp_async.cuh"
 #include "stream2d.h"
+#include "tma.cuh"
 
 namespace fasmg {
 namespace {
@@ -63,9 +67,6 @@ __device__ __forceinline__ StripGeo strip_geo(int nx, int ny, int seg) {
   return g;
 }
 
-__device__ __forceinline__ float4 ld4(const float* base, int64_t off) {
-  return *reinterpret_cast<const float4*>(base + off);
-}
 __device__ __forceinline__ void st4(float* base, int64_t off, float4 v) {
   *reinterpret_cast<float4*>(base + off) = v;
 }
@@ -98,11 +99,11 @@ __device__ __forceinline__ int xflag(const LaneCoef& q) {
 
 __device__ __forceinline__ int yflags(int y, int ny) { return ((y == 0) << 2) | ((y == ny - 1) << 3); }
 
-// Gauss-Seidel update of cell v of the lane (same expression as point_update in common.cuh).
+// Gauss-Seidel update of cell v of the lane from its neighbour sum nb (same expression as
+// point_update in common.cuh).
 template <bool FAST, int V>
-__device__ __forceinline__ float gs(float w, float e, float s, float n, float fv, int yf, const LaneCoef& q,
-                                    const LevelDesc<float>& L, bool in, float old) {
-  const float nb = (w + e) + (s + n);
+__device__ __forceinline__ float gs(float nb, float fv, int yf, const LaneCoef& q, const LevelDesc<float>& L,
+                                    bool in, float old) {
   float a = q.a[V], b = q.b[V];
   if (FAST) return fmaf(a, nb, b * fv);
   if (yf) {
@@ -119,18 +120,20 @@ __device__ __forceinline__ float dcoef(int yf, const LaneCoef& q, const LevelDes
 }
 
 // One colour phase on a row: PAR = 0 updates cells v = 0, 2 of the lane; PAR = 1 cells v = 1, 3.
-template <bool FAST, int PAR>
+// NBZ: every neighbour of the updated cells is zero (the first phase from a zero initial guess: the
+// cells of the other colour have not been touched), so the neighbour sum is +0 without reading them.
+template <bool FAST, int PAR, bool NBZ = false>
 __device__ __forceinline__ void phase_row(float4& c, const float4& s, const float4& n, const float4& fv, int y,
                                           const LaneCoef& q, const LevelDesc<float>& L, bool in) {
   const int yf = FAST ? 0 : yflags(y, L.ny);
   if (PAR == 0) {
-    const float wv = __shfl_up_sync(kFull, c.w, 1);
-    c.x = gs<FAST, 0>(wv, c.y, s.x, n.x, fv.x, yf, q, L, in, c.x);
-    c.z = gs<FAST, 2>(c.y, c.w, s.z, n.z, fv.z, yf, q, L, in, c.z);
+    const float wv = NBZ ? 0.f : __shfl_up_sync(kFull, c.w, 1);
+    c.x = gs<FAST, 0>(NBZ ? 0.f : (wv + c.y) + (s.x + n.x), fv.x, yf, q, L, in, c.x);
+    c.z = gs<FAST, 2>(NBZ ? 0.f : (c.y + c.w) + (s.z + n.z), fv.z, yf, q, L, in, c.z);
   } else {
-    const float ev = __shfl_down_sync(kFull, c.x, 1);
-    c.y = gs<FAST, 1>(c.x, c.z, s.y, n.y, fv.y, yf, q, L, in, c.y);
-    c.w = gs<FAST, 3>(c.z, ev, s.w, n.w, fv.w, yf, q, L, in, c.w);
+    const float ev = NBZ ? 0.f : __shfl_down_sync(kFull, c.x, 1);
+    c.y = gs<FAST, 1>(NBZ ? 0.f : (c.x + c.z) + (s.y + n.y), fv.y, yf, q, L, in, c.y);
+    c.w = gs<FAST, 3>(NBZ ? 0.f : (c.z + ev) + (s.w + n.w), fv.w, yf, q, L, in, c.w);
   }
 }
 
@@ -169,40 +172,62 @@ __device__ __forceinline__ float2 avg_pair(const float4& lo, const float4& hi) {
   return make_float2(((lo.x + lo.y) + (hi.x + hi.y)) * 0.25f, ((lo.z + lo.w) + (hi.z + hi.w)) * 0.25f);
 }
 
-// Rows are prefetched kPF iterations before their first use with per-lane 16-byte cp.async copies into
-// a shared-memory ring of kPF rows per warp (u and f), one commit group per row; cells outside the
-// domain are zero-filled by the copy. Row y is taken from the ring once cp.async.wait_group leaves
-// at most kPF-1 newer groups pending.
-constexpr int kPF = 4;  // divides kWin
+// Rows are prefetched PF iterations before their first use with per-lane 16-byte cp.async copies into
+// a shared-memory ring of PF rows per warp, one commit group per row; cells outside the domain are
+// zero-filled by the copy. Row y is taken from the ring once cp.async.wait_group leaves at most PF-1
+// newer groups pending. PF divides kWin. (Prefetching 8 rows ahead measured slower for every kernel.)
+constexpr int kPF = 4;      // post-smoothing
+constexpr int kPFPre = 4;   // pre-smoothing that reads u
+constexpr int kPFZero = 4;  // pre-smoothing from a zero start (its ring holds f only)
+
+template <int PF, bool HAS_U>
+struct PreRing {
+  static constexpr int kDepth = PF;
+  static constexpr bool kHasC = false;
+  float4 u[HAS_U ? PF : 1][32];
+  float4 f[PF][32];
+};
 
 template <bool UPD>
 struct Ring {
+  static constexpr int kDepth = kPF;
+  static constexpr bool kHasC = true;
   float4 u[kPF][32];
   float4 f[kPF][32];
+  float2 c[kPF][32];  // the coarse values of the row pair that ends at the slot's row
 };
+// The post-smoothing kernel that also updates a float64 field stages each output row's correction e
+// (converted to float64) in shared memory; one lane adds the row to the float64 field with a bulk
+// reduction in the L2 (u64 += e, rounded to nearest), so the kernel never reads u64 itself.
+constexpr int kStage = 2;  // staged rows per warp whose bulk reductions may still be reading
 template <>
-struct Ring<true> {  // the post-smoothing kernel that also updates a float64 field
+struct Ring<true> {
+  static constexpr int kDepth = kPF;
+  static constexpr bool kHasC = true;
   float4 u[kPF][32];
   float4 f[kPF][32];
-  double2 w[kPF][2][32];  // float64 solution row, two halves of the lane's 4 cells
+  float2 c[kPF][32];
+  double e[kStage][128];
 };
 
-// Issue the copies of row y (u only when load_u) into ring slot `slot`, then commit the group.
-template <bool FAST, bool UPD>
-__device__ __forceinline__ void prefetch_row(Ring<UPD>& R, int slot, const float* __restrict__ u,
-                                             const float* __restrict__ f, bool load_u, int y, int ny,
-                                             const StripGeo& g, int nx, const double* __restrict__ w = nullptr,
-                                             int yw = 0) {
+// Issue the copies of row y (u only when LOAD_U) into ring slot `slot`, then commit the group. In
+// the post-smoothing rings (kHasC), a group of an odd row y also holds the lane's two coarse values of
+// the row pair (y - 1, y), zero outside 1 <= y <= min(yend, ny - 1).
+template <bool FAST, bool LOAD_U, typename RingT>
+__device__ __forceinline__ void prefetch_row(RingT& R, int slot, const float* __restrict__ u,
+                                             const float* __restrict__ f, int y, int ny, const StripGeo& g, int nx,
+                                             const float* __restrict__ uc = nullptr, int yend = 0) {
   const int lane = threadIdx.x & 31;
   const bool valid = FAST || (y >= 0 && y < ny && g.lane_in);
   const int64_t off = valid ? (int64_t)y * nx + g.xl : 0;
-  if (load_u) cp_async16(&R.u[slot][lane], u + off, valid);
+  if constexpr (LOAD_U) cp_async16(&R.u[slot][lane], u + off, valid);
   cp_async16(&R.f[slot][lane], f + off, valid);
-  if constexpr (UPD) {  // the float64 row yw of the same lane, for the store stage kPF steps later
-    const bool vw = FAST || (yw >= 0 && yw < ny && g.lane_in);
-    const int64_t ow = vw ? (int64_t)yw * nx + g.xl : 0;
-    cp_async16(&R.w[slot][0][lane], w + ow, vw);
-    cp_async16(&R.w[slot][1][lane], w + ow + 2, vw);
+  if constexpr (RingT::kHasC) {
+    if (y & 1) {
+      const bool vc = y <= yend && y >= 1 && y < ny && g.lane_in;
+      const int64_t oc = vc ? (int64_t)(y >> 1) * (nx >> 1) + (g.xl >> 1) : 0;
+      cp_async8z(&R.c[slot][lane], uc + oc, vc);
+    }
   }
   cp_async_commit();
 }
@@ -211,8 +236,8 @@ __device__ __forceinline__ void prefetch_row(Ring<UPD>& R, int slot, const float
 // loop to whole windows and the prefetch distance) lies in 1..ny-2 and its strip in 1..nx-2: then no
 // row or column test is needed and every cell has the interior stencil constants. Interior warps run
 // the FAST instantiation of the body; the others the general one. Both compute the same values.
-__device__ __forceinline__ bool interior(const StripGeo& g, int ystart, int yend, int nx, int ny) {
-  const int ylast = ystart + ((yend - ystart) / kWin + 1) * kWin - 1 + kPF;
+__device__ __forceinline__ bool interior(const StripGeo& g, int ystart, int yend, int nx, int ny, int pf) {
+  const int ylast = ystart + ((yend - ystart) / kWin + 1) * kWin - 1 + pf;
   return ystart >= 1 && ylast <= ny - 2 && g.x0 >= 1 && g.x0 + 32 * 4 - 1 <= nx - 2;
 }
 
@@ -224,8 +249,11 @@ __device__ __forceinline__ bool interior(const StripGeo& g, int ystart, int yend
 //   uout : u after NS sweeps (output rows)
 //   uc, rc : R(u), R(r) on the next coarser level (nullable: no residual / restriction stage)
 // ------------------------------------------------------------------------------------------------
+template <int NS, bool ZERO, bool TAU>
+using PreRingOf = PreRing<ZERO ? kPFZero : kPFPre, !ZERO>;
+
 template <int NS, bool ZERO, bool TAU, bool FAST>
-__device__ __forceinline__ void pre_body(Ring<false>& R, const StripGeo& g, int ystart, int yend,
+__device__ __forceinline__ void pre_body(PreRingOf<NS, ZERO, TAU>& R, const StripGeo& g, int ystart, int yend,
                                          const float* __restrict__ uin, const float* __restrict__ fin,
                                          float* __restrict__ fout, float* __restrict__ uout, float* __restrict__ uc,
                                          float* __restrict__ rc, const LevelDesc<float>& L) {
@@ -244,18 +272,19 @@ __device__ __forceinline__ void pre_body(Ring<false>& R, const StripGeo& g, int 
     U[k] = rprev;
     F[k] = rprev;
   }
+  constexpr int PF = PreRingOf<NS, ZERO, TAU>::kDepth;
 #pragma unroll
-  for (int k = 0; k < kPF; ++k) prefetch_row<FAST, false>(R, k, uin, fin, !ZERO, ystart + k, ny, g, nx);
+  for (int k = 0; k < PF; ++k) prefetch_row<FAST, !ZERO>(R, k, uin, fin, ystart + k, ny, g, nx);
   const int nxc = nx >> 1;
   for (int yb = ystart; yb <= yend; yb += kWin) {
 #pragma unroll
     for (int it = 0; it < kWin; ++it) {
       const int y = yb + it;
-      // ---- take row y from the ring, prefetch row y + kPF into its slot
-      cp_async_wait<kPF - 1>();
-      U[it] = ZERO ? make_float4(0.f, 0.f, 0.f, 0.f) : R.u[it % kPF][lane];
-      F[it] = R.f[it % kPF][lane];
-      prefetch_row<FAST, false>(R, it % kPF, uin, fin, !ZERO, y + kPF, ny, g, nx);
+      // ---- take row y from the ring, prefetch row y + PF into its slot
+      cp_async_wait<PF - 1>();
+      U[it] = ZERO ? make_float4(0.f, 0.f, 0.f, 0.f) : R.u[it % PF][lane];
+      F[it] = R.f[it % PF][lane];
+      prefetch_row<FAST, !ZERO>(R, it % PF, uin, fin, y + PF, ny, g, nx);
       // ---- tau: f = R(r) + A u at row y-1 (u still the restricted start)
       if (TAU) {
         const int yt = y - 1;
@@ -278,10 +307,16 @@ __device__ __forceinline__ void pre_body(Ring<false>& R, const StripGeo& g, int 
           const int s = (it - LT - t) & M;
           // colour 1 (t odd): cells with (x + y) odd, i.e. v = (y+1)&1; colour 0: v = y&1
           const int par = (t & 1) ? ((it - LT - t + 1) & 1) : ((it - LT - t) & 1);
-          if (par == 0)
+          if (ZERO && t == 1) {  // colour 1 from a zero start: its neighbours are all still zero
+            if (par == 0)
+              phase_row<FAST, 0, true>(U[s], U[(s - 1) & M], U[(s + 1) & M], F[s], yp, q, L, g.lane_in);
+            else
+              phase_row<FAST, 1, true>(U[s], U[(s - 1) & M], U[(s + 1) & M], F[s], yp, q, L, g.lane_in);
+          } else if (par == 0) {
             phase_row<FAST, 0>(U[s], U[(s - 1) & M], U[(s + 1) & M], F[s], yp, q, L, g.lane_in);
-          else
+          } else {
             phase_row<FAST, 1>(U[s], U[(s - 1) & M], U[(s + 1) & M], F[s], yp, q, L, g.lane_in);
+          }
         }
       }
       // ---- store u, residual and restriction at row y - LR
@@ -318,14 +353,15 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr int NP = 2 * NS;
   constexpr int LT = TAU ? 1 : 0;
   extern __shared__ __align__(16) unsigned char ring_smem[];
-  Ring<false>* rings = reinterpret_cast<Ring<false>*>(ring_smem);
+  using RingT = PreRingOf<NS, ZERO, TAU>;
+  RingT* rings = reinterpret_cast<RingT*>(ring_smem);
   const StripGeo g = strip_geo(L.nx, L.ny, seg);
   if (g.y0 >= L.ny) return;  // whole warp: surplus warps of the last block
   const int ytop = g.y0 - (NP + 1 + LT);                                    // first row that must be loaded
   const int ystart = (ytop >= 0 ? ytop : ytop - (kWin - 1)) / kWin * kWin;  // floor to kWin
   const int yend = g.y1 + (uc != nullptr ? NP + 1 + LT : NP + LT);         // last pipeline row
-  Ring<false>& R = rings[threadIdx.x >> 5];
-  if (interior(g, ystart, yend, L.nx, L.ny))
+  RingT& R = rings[threadIdx.x >> 5];
+  if (interior(g, ystart, yend, L.nx, L.ny, RingT::kDepth))
     pre_body<NS, ZERO, TAU, true>(R, g, ystart, yend, uin, fin, fout, uout, uc, rc, L);
   else
     pre_body<NS, ZERO, TAU, false>(R, g, ystart, yend, uin, fin, fout, uout, uc, rc, L);
@@ -352,16 +388,10 @@ __device__ __forceinline__ void post_body(Ring<UPD>& R, const StripGeo& g, int y
     F[k] = U[k];
   }
 #pragma unroll
-  for (int k = 0; k < kPF; ++k)
-    prefetch_row<FAST, UPD>(R, k, uin, f, true, ystart + k, ny, g, nx, u64, ystart + k - LW);
-  const int nxc = nx >> 1;
-  // coarse values of the next row pair, loaded one pair ahead of their use (rows y-1, y with y odd)
-  auto load_uc = [&](int yy) {
-    return (yy <= yend && yy >= 1 && yy < ny && g.lane_in)
-               ? *reinterpret_cast<const float2*>(uc + (int64_t)(yy >> 1) * nxc + (g.xl >> 1))
-               : make_float2(0.f, 0.f);
-  };
-  float2 cvn = load_uc(ystart + 1);  // ystart is even
+  for (int k = 0; k < kPF; ++k) prefetch_row<FAST, true>(R, k, uin, f, ystart + k, ny, g, nx, uc, yend);
+  // UPD: the output lanes are 2 .. 2 + nout - 1 (the strip's first output column x0 + 8 is >= 0)
+  const int nout = min((kStripHalo + kStripOut) / 4, (nx - g.x0) / 4) - kStripHalo / 4;
+  int stage = 0;
   for (int yb = ystart; yb <= yend; yb += kWin) {
 #pragma unroll
     for (int it = 0; it < kWin; ++it) {
@@ -369,21 +399,13 @@ __device__ __forceinline__ void post_body(Ring<UPD>& R, const StripGeo& g, int y
       cp_async_wait<kPF - 1>();
       U[it] = R.u[it % kPF][lane];
       F[it] = R.f[it % kPF][lane];
-      // UPD: the float64 solution row stored at the end of this step (row y - LW)
-      double2 ua = make_double2(0.0, 0.0), ub = ua;
-      if constexpr (UPD) {
-        ua = R.w[it % kPF][0][lane];
-        ub = R.w[it % kPF][1][lane];
-      }
-      prefetch_row<FAST, UPD>(R, it % kPF, uin, f, true, y + kPF, ny, g, nx, u64, y + kPF - LW);
+      // coarse-grid correction values of the row pair (y-1, y) (ystart is even: y odd when it is odd)
+      const float2 cv = (it & 1) ? R.c[it % kPF][lane] : make_float2(0.f, 0.f);
+      prefetch_row<FAST, true>(R, it % kPF, uin, f, y + kPF, ny, g, nx, uc, yend);
       const int yw = y - LW;
-      const bool wr = yw >= g.y0 && yw < g.y1 && g.lane_out;
+      const bool row_out = yw >= g.y0 && yw < g.y1;  // warp-uniform
+      const bool wr = row_out && g.lane_out;
       // coarse-grid correction of the row pair (y-1, y)
-      float2 cv = make_float2(0.f, 0.f);
-      if ((it & 1) == 1) {
-        cv = cvn;
-        cvn = load_uc(y + 2);
-      }
       if ((it & 1) == 1 && (FAST || (y < ny && y >= 1 && g.lane_in))) {
         float4& lo = U[(it - 1) & M];
         float4& hi = U[it];
@@ -410,23 +432,34 @@ __device__ __forceinline__ void post_body(Ring<UPD>& R, const StripGeo& g, int y
             phase_row<FAST, 1>(U[s], U[(s - 1) & M], U[(s + 1) & M], F[s], yp, q, L, g.lane_in);
         }
       }
-      if (wr) {
-        const float4 e = U[(it - LW) & M];
-        if (UPD) {  // mixed precision: u64 += e, the float64 update of the refinement step
-          double2* dst = reinterpret_cast<double2*>(u64 + (int64_t)yw * nx + g.xl);
-          ua.x += f32_to_f64_bits(e.x);
-          ua.y += f32_to_f64_bits(e.y);
-          ub.x += f32_to_f64_bits(e.z);
-          ub.y += f32_to_f64_bits(e.w);
-          dst[0] = ua;
-          dst[1] = ub;
-        } else {
-          st4(uout, (int64_t)yw * nx + g.xl, e);
+      if constexpr (UPD) {  // mixed precision: u64 += e, the float64 update of the refinement step
+        if (row_out) {
+          double* st = R.e[stage];
+          stage = (stage + 1) & (kStage - 1);
+          if (lane == 0) bulk_wait_read<kStage - 1>();  // the slot's previous reduction has read it
+          __syncwarp();
+          if (g.lane_out) {
+            const float4 e = U[(it - LW) & M];
+            double2* d = reinterpret_cast<double2*>(st + 4 * lane);
+            d[0] = make_double2(f32_to_f64_bits(e.x), f32_to_f64_bits(e.y));
+            d[1] = make_double2(f32_to_f64_bits(e.z), f32_to_f64_bits(e.w));
+          }
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            bulk_reduce_add_f64(u64 + (int64_t)yw * nx + g.x0 + kStripHalo, st + kStripHalo, (uint32_t)nout * 32u);
+            bulk_commit();
+          }
         }
+      } else if (wr) {
+        st4(uout, (int64_t)yw * nx + g.xl, U[(it - LW) & M]);
       }
     }
   }
   cp_async_wait_all();
+  if constexpr (UPD) {
+    if (lane == 0) bulk_wait_all();
+  }
 }
 
 template <int NS, bool UPD>
@@ -443,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int ystart = (ytop >= 0 ? ytop : ytop - (kWin - 1)) / kWin * kWin;
   const int yend = g.y1 + NP + 1;
   Ring<UPD>& R = rings[threadIdx.x >> 5];
-  if (interior(g, ystart, yend, L.nx, L.ny))
+  if (interior(g, ystart, yend, L.nx, L.ny, Ring<UPD>::kDepth))
     post_body<NS, true, UPD>(R, g, ystart, yend, uin, f, uc, uout, u64, L);
   else
     post_body<NS, false, UPD>(R, g, ystart, yend, uin, f, uc, uout, u64, L);
@@ -463,7 +496,7 @@ bool stream2d_supported(int nx, int ny, int nu) {
 }
 
 #define PRE_CASE(NSV, Z, T)                                                                      \
-  k_pre<NSV, Z, T><<<blocks_for(L.nx, L.ny, seg), kThreads, sizeof(Ring<false>) * kWarps, stream>>>( \
+  k_pre<NSV, Z, T><<<blocks_for(L.nx, L.ny, seg), kThreads, sizeof(PreRingOf<NSV, Z, T>) * kWarps, stream>>>( \
       uin, fin, fout, uout, uc, rc, L, seg)
 
 cudaError_t launch_stream2d_pre(const float* uin, const float* fin, float* fout, float* uout, float* uc, float* rc,
@@ -487,6 +520,17 @@ cudaError_t launch_stream2d_pre(const float* uin, const float* fin, float* fout,
   return cudaGetLastError();
 }
 
+template <int NS>
+cudaError_t pre_attr() {
+  const auto a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_pre<NS, true, false>, a, (int)(sizeof(PreRingOf<NS, true, false>) * kWarps));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pre<NS, false, false>, a, (int)(sizeof(PreRingOf<NS, false, false>) * kWarps));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pre<NS, false, true>, a, (int)(sizeof(PreRingOf<NS, false, true>) * kWarps));
+  return e;
+}
+
 // Shared-memory size attributes of every fused kernel, set once before any launch or stream capture.
 cudaError_t stream2d_prepare() {
   static std::once_flag once;
@@ -495,6 +539,8 @@ cudaError_t stream2d_prepare() {
     const int big = (int)(sizeof(Ring<true>) * kWarps);
     cudaError_t e = cudaFuncSetAttribute(k_post<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_post<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = pre_attr<1>();
+    if (e == cudaSuccess) e = pre_attr<2>();
     err = e;
   });
   return err;

@@ -77,6 +77,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
+// Bulk reduction of `bytes` bytes (a multiple of 16; both addresses 16-byte aligned) of float64 values
+// from shared memory into global memory: dst[i] += src[i], each sum rounded to nearest in the L2. The
+// copy joins this thread's current bulk group (commit with bulk_commit).
+__device__ __forceinline__ void bulk_reduce_add_f64(double* dst, const double* src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until at most N of this thread's bulk groups still read their shared-memory source.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// Wait until every bulk group of this thread has completed (its writes are performed).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Host: a rank-3 tensor map of a dense float64 or float32 field (elem_bytes 8 or 4, x fastest) with
 // box (bx, by, bz); out-of-range elements of a tile load read as zero. Returns cudaErrorInvalidValue
 // when the driver rejects the description (alignment, sizes), cudaErrorNotSupported without the

@@ -342,6 +342,8 @@ def run_ours(args, ws, rank, local):
             hb = rf if rf["bound"] == "hbm" else rf["hbm"]
             xm[name] = {"ms_per_launch": r["ms"] / r["launches"],
                         "kernel_GBs": hb["achieved"], "kernel_frac": hb["frac"],
+                        "algorithmic_bytes_per_cell": hb["algorithmic_bytes_per_cell"],
+                        "traffic_bytes_per_cell": traffic_table().get("%s@0" % fam),
                         "sweep_equiv_GBs": 2 * 3 * 4 * cells / t / 1e9}
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside the region)

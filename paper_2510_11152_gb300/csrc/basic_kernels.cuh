@@ -305,13 +305,13 @@ template <typename T, int DIM, bool PER>
 __device__ __forceinline__ void smooth_colour4_body(T* u, const T* f, const LevelDesc<T>& L, int colour) {
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int64_t sy = nx, sz = (int64_t)nx * ny;
-  const int gpr = nx >> 2;  // groups per row
-  const int64_t ngroups = (int64_t)gpr * ny * nz;
+  const int lg = L.lx - 2;  // groups per row: nx / 4 = 2^lg (every extent is a power of two)
+  const int64_t ngroups = (int64_t)1 << (lg + L.ly + L.lz);
   for (int64_t g = gtid(); g < ngroups; g += gstride()) {
-    const int x0 = (int)(g % gpr) << 2;
-    const int64_t rest = g / gpr;
-    const int j = (int)(rest % ny);
-    const int l = (int)(rest / ny);
+    const int x0 = (int)(g & ((1 << lg) - 1)) << 2;
+    const int64_t rest = g >> lg;
+    const int j = (int)(rest & (ny - 1));
+    const int l = (int)(rest >> L.ly);
     const int64_t idx = ((int64_t)l * ny + j) * nx + x0;
     Quad<T> c, s4, n4, b4, t4, f4;
     c.ld(u + idx);

@@ -64,6 +64,8 @@ bool is_pow2(int n) { return n >= 1 && (n & (n - 1)) == 0; }
 constexpr int kBlock = 256;
 constexpr int kCoarseThreads = 1024;
 constexpr int64_t kSwitchCells2D = 16384;  // levels at or below this size run in one CTA
+constexpr int64_t kSwitchCells2DLarge = 4096;  // the same on 2D grids of at least kLargeGrid2D cells
+constexpr int64_t kLargeGrid2D = (int64_t)1 << 24;
 constexpr int64_t kSwitchCells3D = 4096;
 constexpr size_t kCoarseSmemMax = 200 * 1024;    // field arrays of the single-CTA kernel
 constexpr size_t kCoarseSmemLimit = 227 * 1024;  // with its level descriptors (per-CTA maximum)
@@ -274,8 +276,13 @@ fas_status build_hier(fas_ctx* c, Hier<T>& H, bool buffers, bool level0_buffers)
   H.desc.clear();
   for (int l = 0; l < c->nlev; ++l) H.desc.push_back(make_desc<T>(p, c->shape[l]));
   // single-CTA switch level: the first level small enough that the GPU cannot be filled and whose
-  // whole sub-hierarchy (u, f on every level, u0 below it) fits in the CTA's shared memory
-  const int64_t sw_cells = p.dim == 2 ? kSwitchCells2D : kSwitchCells3D;
+  // whole sub-hierarchy (u, f on every level, u0 below it) fits in the CTA's shared memory. On a
+  // large 2D grid nothing else runs beside the small levels, and one CTA smoothing 128^2 is slower than
+  // per-operation launches across the GPU (8192^2: 118.1 -> 116.1 ms per 20-step run with the switch
+  // at 64^2); smaller grids, often solved side by side in a batch, keep the switch at 128^2 (the
+  // 96-problem batch was 2 % slower with 64^2).
+  const int64_t sw_cells =
+      p.dim == 2 ? (c->shape[0].cells() >= kLargeGrid2D ? kSwitchCells2DLarge : kSwitchCells2D) : kSwitchCells3D;
   H.switch_level = c->nlev - 1;
   for (int l = 0; l < c->nlev; ++l) {
     if (c->shape[l].cells() > sw_cells) continue;

@@ -225,6 +225,50 @@ def test_singular_poisson_coarse_exact(cuda_lib):
     assert _rel(_n(ug), u_ref) <= 1e-10
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_zero_right_hand_side(cuda_lib, precision):
+    """f = 0. From u = 0 the solve returns u = 0 exactly after one cycle: the relative test falls back
+    to the initial residual, which is 0. From a nonzero guess it drives the residual 1e10 times below
+    the initial one (the oracle evaluates both residuals)."""
+    fas = cuda_lib
+    shape = (128, 128)
+    op, ctx = _pair(fas, shape, 1.0 / 128, 1.0, 1e-3, 1.0, (N_,) * 4, coarsest=4, precision=precision)
+    zero = np.zeros(shape)
+    u = _t(zero)
+    info = fas.fas_solve(ctx, u, _t(zero))
+    assert info.converged and info.cycles == 1
+    assert not np.any(_n(u))
+    u0 = random_field(shape, 271, -1, 1)
+    u = _t(u0)
+    info = fas.fas_solve(ctx, u, _t(zero))
+    assert info.converged
+    r0 = cc.norm2(cc.residual(op, u0, zero))
+    assert cc.norm2(cc.residual(op, _n(u), zero)) <= 1e-10 * r0 * (1 + 1e-5)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("shape,coarsest,exact", [((2, 2), 2, True), ((4, 4), 2, False), ((2, 16), 2, True),
+                                                  ((4, 256), 4, True), ((2, 2, 2), 2, True), ((4, 4, 4), 2, False),
+                                                  ((2, 4, 8), 2, True)])
+def test_smallest_and_thinnest_grids(cuda_lib, precision, shape, coarsest, exact):
+    """Grids of one level (2 x 2, 2 x 16, 4 x 256: the shortest axis is already the coarsest size) and
+    two levels, smoothed or solved exactly on the coarsest: the GPU solve to 1e-12 against the oracle's
+    to 1e-13, within 1e-10 relative max-norm."""
+    fas = cuda_lib
+    h = 1.0 / shape[-1]
+    bc = (D_, N_, N_, D_, N_, D_)[: 2 * len(shape)]
+    op, ctx = _pair(fas, shape, h, 1.0, 1e-2, 1.0, bc, coarsest=coarsest, coarse_exact=int(exact),
+                    precision=precision, tol=1e-12, kmax=100)
+    f = random_field(shape, 281, -1, 1)
+    u_ref = np.zeros(shape)
+    cc.solve(cc.build_levels(op, coarsest), u_ref, f,
+             cc.Params(tol=1e-13, kmax=200, coarsest=coarsest, coarse_exact=exact))
+    ug = _t(np.zeros(shape))
+    info = fas.fas_solve(ctx, ug, _t(f))
+    assert info.converged
+    assert _rel(_n(ug), u_ref) <= 1e-10
+
+
 def test_error_statuses(cuda_lib):
     import torch
     fas = cuda_lib

@@ -699,6 +699,80 @@ __global__ void k_restrict_resid(T* uc, T* uc0, T* fc, const T* u, const T* f, L
     restrict_resid_face_range<T, DIM, FAX>(uc, uc0, fc, u, f, L, gtid(), gstride());
 }
 
+// 3D float32 cell levels with constant kappa, no periodic axis and a multiple of 4 cells per row: the
+// residual-restriction of k_restrict_resid with one thread per 4 x 2 x 2 block of fine cells (two
+// coarse cells), every row of the block and of its y and z neighbours read as one 16-byte vector.
+// Each residual is residual_point's expression and R(u), R(r) use avg_children's association, so the
+// results are those of k_restrict_resid bit for bit.
+static __global__ void __launch_bounds__(256) k_restrict_resid4_3d(float* __restrict__ uc, float* __restrict__ uc0,
+                                                            float* __restrict__ fc, const float* __restrict__ u,
+                                                            const float* __restrict__ f, const LevelDesc<float> L) {
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  const int lg = L.lx - 2;
+  const int64_t ngroups = (int64_t)1 << (lg + L.ly - 1 + L.lz - 1);
+  for (int64_t g = gtid(); g < ngroups; g += gstride()) {
+    const int x0 = (int)(g & ((1 << lg) - 1)) << 2;
+    const int64_t rest = g >> lg;
+    const int j0 = (int)(rest & ((ny >> 1) - 1)) << 1;
+    const int l0 = (int)(rest >> (L.ly - 1)) << 1;
+    const int64_t base = ((int64_t)l0 * ny + j0) * nx + x0;
+    Quad<float> c[2][2], fq[2][2], sq[2], nq[2], bq[2], tq[2];  // [dl][dj]; y neighbours per dl; z per dj
+    float we[2][2], ee[2][2];
+#pragma unroll
+    for (int dl = 0; dl < 2; ++dl)
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj) {
+        const int64_t q = base + dl * sz + dj * sy;
+        c[dl][dj].ld(u + q);
+        fq[dl][dj].ld(f + q);
+        we[dl][dj] = x0 > 0 ? u[q - 1] : 0.f;
+        ee[dl][dj] = x0 + 4 < nx ? u[q + 4] : 0.f;
+      }
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      sq[d].v[0] = sq[d].v[1] = sq[d].v[2] = sq[d].v[3] = 0.f;
+      nq[d] = sq[d];
+      bq[d] = sq[d];
+      tq[d] = sq[d];
+      if (j0 > 0) sq[d].ld(u + base + d * sz - sy);
+      if (j0 + 2 < ny) nq[d].ld(u + base + d * sz + 2 * sy);
+      if (l0 > 0) bq[d].ld(u + base + d * sy - sz);
+      if (l0 + 2 < nz) tq[d].ld(u + base + d * sy + 2 * sz);
+    }
+    float r[2][2][4];
+#pragma unroll
+    for (int dl = 0; dl < 2; ++dl)
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float w = k > 0 ? c[dl][dj].v[k > 0 ? k - 1 : 0] : we[dl][dj];
+          const float e = k < 3 ? c[dl][dj].v[k < 3 ? k + 1 : 3] : ee[dl][dj];
+          const float sv = dj == 0 ? sq[dl].v[k] : c[dl][0].v[k];
+          const float nv = dj == 0 ? c[dl][1].v[k] : nq[dl].v[k];
+          const float bo = dl == 0 ? bq[dj].v[k] : c[0][dj].v[k];
+          const float to = dl == 0 ? c[1][dj].v[k] : tq[dj].v[k];
+          const float acc = ((w + e) + (sv + nv)) + (bo + to);
+          const int cls = bclass<3>(x0 + k, j0 + dj, l0 + dl, nx, ny, nz);
+          r[dl][dj][k] = fmaf(L.c, acc, fmaf(-L.d[cls], c[dl][dj].v[k], fq[dl][dj].v[k]));
+        }
+    const int64_t I = ((int64_t)(l0 >> 1) * (ny >> 1) + (j0 >> 1)) * (nx >> 1) + (x0 >> 1);
+#pragma unroll
+    for (int qc = 0; qc < 2; ++qc) {
+      const int a = 2 * qc, b = 2 * qc + 1;
+      const float s1 = (c[0][0].v[a] + c[0][0].v[b]) + (c[0][1].v[a] + c[0][1].v[b]);
+      const float s2 = (c[1][0].v[a] + c[1][0].v[b]) + (c[1][1].v[a] + c[1][1].v[b]);
+      const float v = (s1 + s2) * 0.125f;
+      uc[I + qc] = v;
+      uc0[I + qc] = v;
+      const float r1 = (r[0][0][a] + r[0][0][b]) + (r[0][1][a] + r[0][1][b]);
+      const float r2 = (r[1][0][a] + r[1][0][b]) + (r[1][1][a] + r[1][1][b]);
+      fc[I + qc] = (r1 + r2) * 0.125f;
+    }
+  }
+}
+
 // The single-CTA V-cycle's work once its descriptors are in shared memory (sdesc, indexed by level).
 template <typename T, int DIM, int FAX, bool PER>
 __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& A, const SmemLayout& S, T* utop, const T* ftop, T* sm,

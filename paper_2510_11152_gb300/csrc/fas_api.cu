@@ -584,7 +584,15 @@ fas_status vcycle_basic_from(fas_ctx* c, Hier<T>& H, int lfrom, T* utop, const T
     const int64_t nc = n >> DIM;
     {  // residual and its restriction in one pass (the residual is not stored)
       Prof pr(c, FAS_K_RESTRICT, l, (double)n);
-      with_fax(c, [&](auto tag) {
+      bool blocks = false;  // 3D float32 cell levels: 4 x 2 x 2 fine cells per thread (path 1: one per cell)
+      if constexpr (std::is_same<T, float>::value && DIM == 3) {
+        if (c->p.path != 1 && L.fax < 0 && !L.per && !L.varkappa && (L.nx & 3) == 0) {
+          k_restrict_resid4_3d<<<grid_for(c, nc / 2), kBlock, 0, c->stream>>>(H.u[l + 1], H.u0[l + 1], H.f[l + 1],
+                                                                             u, f, L);
+          blocks = true;
+        }
+      }
+      if (!blocks) with_fax(c, [&](auto tag) {
         constexpr int FAX = decltype(tag)::value;
         k_restrict_resid<T, DIM, FAX><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.u[l + 1], H.u0[l + 1],
                                                                                  H.f[l + 1], u, f, L);

@@ -448,7 +448,21 @@ static __global__ void k_heat_rhs(double* b, const double* u, const double* fsrc
 
 // ---- mixed precision (iterative refinement): u += e, and r32 = (float)(b - A u) with its norm
 static __global__ void k_ir_update(double* u, const float* e, int64_t n) {
-  for (int64_t i = gtid(); i < n; i += gstride()) u[i] += f32_to_f64_bits(e[i]);
+  // four cells per iteration (one 16-byte load of e, two of u; both fields 16-byte aligned), then the
+  // remaining n % 4 one by one
+  const int64_t n4 = n >> 2;
+  for (int64_t i = gtid(); i < n4; i += gstride()) {
+    const float4 ev = reinterpret_cast<const float4*>(e)[i];
+    double2* up = reinterpret_cast<double2*>(u) + 2 * i;
+    double2 a = up[0], b = up[1];
+    a.x += f32_to_f64_bits(ev.x);
+    a.y += f32_to_f64_bits(ev.y);
+    b.x += f32_to_f64_bits(ev.z);
+    b.y += f32_to_f64_bits(ev.w);
+    up[0] = a;
+    up[1] = b;
+  }
+  for (int64_t i = 4 * n4 + gtid(); i < n; i += gstride()) u[i] += f32_to_f64_bits(e[i]);
 }
 
 // Bit patterns of the neighbours of cell (i, j, l) in the order x-, x+, y-, y+, z-, z+ (0 where a
@@ -770,6 +784,43 @@ static __global__ void __launch_bounds__(256) k_restrict_resid4_3d(float* __rest
       const float r2 = (r[1][0][a] + r[1][0][b]) + (r[1][1][a] + r[1][1][b]);
       fc[I + qc] = (r1 + r2) * 0.125f;
     }
+  }
+}
+
+// The tau correction fc += A_c uc on the same kind of 3D float32 level, 4 cells per thread
+// (apply_point's expression per cell, so the results equal k_tau's).
+static __global__ void __launch_bounds__(256) k_tau4_3d(float* __restrict__ fc, const float* __restrict__ uc,
+                                                        const LevelDesc<float> L) {
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  const int lg = L.lx - 2;
+  const int64_t ngroups = (int64_t)1 << (lg + L.ly + L.lz);
+  for (int64_t g = gtid(); g < ngroups; g += gstride()) {
+    const int x0 = (int)(g & ((1 << lg) - 1)) << 2;
+    const int64_t rest = g >> lg;
+    const int j = (int)(rest & (ny - 1));
+    const int l = (int)(rest >> L.ly);
+    const int64_t idx = ((int64_t)l * ny + j) * nx + x0;
+    Quad<float> c, fq, sq, nq, bq, tq;
+    c.ld(uc + idx);
+    fq.ld(fc + idx);
+    sq.v[0] = sq.v[1] = sq.v[2] = sq.v[3] = 0.f;
+    nq = sq;
+    bq = sq;
+    tq = sq;
+    if (j > 0) sq.ld(uc + idx - sy);
+    if (j < ny - 1) nq.ld(uc + idx + sy);
+    if (l > 0) bq.ld(uc + idx - sz);
+    if (l < nz - 1) tq.ld(uc + idx + sz);
+    const float we = x0 > 0 ? uc[idx - 1] : 0.f, ee = x0 + 4 < nx ? uc[idx + 4] : 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float w = k > 0 ? c.v[k > 0 ? k - 1 : 0] : we, e = k < 3 ? c.v[k < 3 ? k + 1 : 3] : ee;
+      const float acc = ((w + e) + (sq.v[k] + nq.v[k])) + (bq.v[k] + tq.v[k]);
+      const int cls = bclass<3>(x0 + k, j, l, nx, ny, nz);
+      fq.v[k] = fq.v[k] + fmaf(L.d[cls], c.v[k], -L.c * acc);
+    }
+    fq.st(fc + idx);
   }
 }
 

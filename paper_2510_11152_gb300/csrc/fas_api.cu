@@ -600,7 +600,15 @@ fas_status vcycle_basic_from(fas_ctx* c, Hier<T>& H, int lfrom, T* utop, const T
     }
     {
       Prof pr(c, FAS_K_TAU, l + 1, (double)nc);
-      k_tau<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.f[l + 1], H.u[l + 1], H.desc[l + 1]);
+      const LevelDesc<T>& Lc = H.desc[l + 1];
+      bool groups = false;  // 3D float32 cell levels: 4 cells per thread (path 1: one per cell)
+      if constexpr (std::is_same<T, float>::value && DIM == 3) {
+        if (c->p.path != 1 && Lc.fax < 0 && !Lc.per && !Lc.varkappa && (Lc.nx & 3) == 0) {
+          k_tau4_3d<<<grid_for(c, nc / 4), kBlock, 0, c->stream>>>(H.f[l + 1], H.u[l + 1], Lc);
+          groups = true;
+        }
+      }
+      if (!groups) k_tau<T, DIM><<<grid_for(c, nc), kBlock, 0, c->stream>>>(H.f[l + 1], H.u[l + 1], Lc);
     }
   }
   STATUS_TRY((launch_coarse<T, DIM>(c, H, sw, sw == lfrom ? utop : H.u[sw], sw == lfrom ? ftop : H.f[sw])));
@@ -756,7 +764,7 @@ fas_status mixed_step(fas_ctx* c, double* u) {
     CUDA_TRY(cudaMemsetAsync(H.u[0], 0, n * sizeof(float), c->stream));
     for (int k = 0; k < inner; ++k) STATUS_TRY(vcycle<float>(c, H, H.u[0], H.f[0]));
     Prof pr(c, FAS_K_UPDATE, 0, (double)n);
-    k_ir_update<<<grid_for(c, n), kBlock, 0, c->stream>>>(u, H.u[0], n);
+    k_ir_update<<<grid_for(c, (n + 3) / 4), kBlock, 0, c->stream>>>(u, H.u[0], n);
   }
   return FAS_OK;
 }

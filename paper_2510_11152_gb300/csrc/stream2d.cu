@@ -19,7 +19,8 @@
 // see the other colour, so stage t at row y reads rows y-1, y, y+1 after stage t-1, which the
 // pipeline guarantees. West/east neighbours come from the lane itself or by one warp shuffle.
 //
-// Strips and segments overlap (8 columns each side, 5-7 rows at the top and bottom) and recompute
+// Strips and segments overlap (8 columns each side, 4 in the post-smoothing kernel with the float64
+// update; 5-7 rows at the top and bottom) and recompute
 // their halos; only the interior is written. Because neighbours read the halo, nothing a warp reads
 // may be written by this kernel: u is read from one buffer and written to another, and the tau
 // right-hand side is kept in registers and written to a buffer separate from R(r).
@@ -51,19 +52,29 @@ struct StripGeo {
   bool lane_out;  // the lane writes its 4 columns
 };
 
+// HALO recomputed columns on each side of a 128-column strip: the pre-smoothing kernel needs
+// kStripHalo (its residual and restriction read one column beyond the last colour phase); the
+// post-smoothing kernel, whose last stage is the last colour phase, needs one column per phase. Its
+// float64-update variant uses 4 (0.33 -> 0.32 ms per 8192^2 launch); the plain variant measured
+// slower with 4 than with 8 (0.158 -> 0.170 ms) and keeps 8.
+template <bool UPD>
+constexpr int post_halo() { return UPD ? 4 : kStripHalo; }
+
+template <int HALO>
 __device__ __forceinline__ StripGeo strip_geo(int nx, int ny, int seg) {
+  constexpr int OUT = 128 - 2 * HALO;
   const int warp = (blockIdx.x * kWarps) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  const int nstrips = (nx + kStripOut - 1) / kStripOut;
+  const int nstrips = (nx + OUT - 1) / OUT;
   const int strip = warp % nstrips;
   const int sg = warp / nstrips;
   StripGeo g;
-  g.x0 = strip * kStripOut - kStripHalo;
+  g.x0 = strip * OUT - HALO;
   g.xl = g.x0 + 4 * lane;
   g.y0 = sg * seg;
   g.y1 = min(g.y0 + seg, ny);
   g.lane_in = g.xl >= 0 && g.xl < nx;  // nx is a multiple of 4, so all 4 or none
-  g.lane_out = g.lane_in && lane >= kStripHalo / 4 && lane < (kStripHalo + kStripOut) / 4;
+  g.lane_out = g.lane_in && lane >= HALO / 4 && lane < (HALO + OUT) / 4;
   return g;
 }
 
@@ -355,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   extern __shared__ __align__(16) unsigned char ring_smem[];
   using RingT = PreRingOf<NS, ZERO, TAU>;
   RingT* rings = reinterpret_cast<RingT*>(ring_smem);
-  const StripGeo g = strip_geo(L.nx, L.ny, seg);
+  const StripGeo g = strip_geo<kStripHalo>(L.nx, L.ny, seg);
   if (g.y0 >= L.ny) return;  // whole warp: surplus warps of the last block
   const int ytop = g.y0 - (NP + 1 + LT);                                    // first row that must be loaded
   const int ystart = (ytop >= 0 ? ytop : ytop - (kWin - 1)) / kWin * kWin;  // floor to kWin
@@ -389,8 +400,9 @@ __device__ __forceinline__ void post_body(Ring<UPD>& R, const StripGeo& g, int y
   }
 #pragma unroll
   for (int k = 0; k < kPF; ++k) prefetch_row<FAST, true>(R, k, uin, f, ystart + k, ny, g, nx, uc, yend);
-  // UPD: the output lanes are 2 .. 2 + nout - 1 (the strip's first output column x0 + 8 is >= 0)
-  const int nout = min((kStripHalo + kStripOut) / 4, (nx - g.x0) / 4) - kStripHalo / 4;
+  // UPD: the output lanes are H/4 .. H/4 + nout - 1 (the strip's first output column x0 + H is >= 0)
+  constexpr int H = post_halo<UPD>();
+  const int nout = min((128 - H) / 4, (nx - g.x0) / 4) - H / 4;
   int stage = 0;
   for (int yb = ystart; yb <= yend; yb += kWin) {
 #pragma unroll
@@ -447,7 +459,7 @@ __device__ __forceinline__ void post_body(Ring<UPD>& R, const StripGeo& g, int y
           fence_async_smem();
           __syncwarp();
           if (lane == 0) {
-            bulk_reduce_add_f64(u64 + (int64_t)yw * nx + g.x0 + kStripHalo, st + kStripHalo, (uint32_t)nout * 32u);
+            bulk_reduce_add_f64(u64 + (int64_t)yw * nx + g.x0 + H, st + H, (uint32_t)nout * 32u);
             bulk_commit();
           }
         }
@@ -470,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr int NP = 2 * NS;
   extern __shared__ __align__(16) unsigned char ring_smem[];
   Ring<UPD>* rings = reinterpret_cast<Ring<UPD>*>(ring_smem);
-  const StripGeo g = strip_geo(L.nx, L.ny, seg);
+  const StripGeo g = strip_geo<post_halo<UPD>()>(L.nx, L.ny, seg);
   if (g.y0 >= L.ny) return;
   const int ytop = g.y0 - NP;  // even, so correction pairs stay aligned
   const int ystart = (ytop >= 0 ? ytop : ytop - (kWin - 1)) / kWin * kWin;
@@ -482,8 +494,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     post_body<NS, false, UPD>(R, g, ystart, yend, uin, f, uc, uout, u64, L);
 }
 
+template <int HALO>
 int blocks_for(int nx, int ny, int seg) {
-  const int nstrips = (nx + kStripOut - 1) / kStripOut;
+  const int nstrips = (nx + (128 - 2 * HALO) - 1) / (128 - 2 * HALO);
   const int nsegs = (ny + seg - 1) / seg;
   return (nstrips * nsegs + kWarps - 1) / kWarps;
 }
@@ -496,7 +509,7 @@ bool stream2d_supported(int nx, int ny, int nu) {
 }
 
 #define PRE_CASE(NSV, Z, T)                                                                      \
-  k_pre<NSV, Z, T><<<blocks_for(L.nx, L.ny, seg), kThreads, sizeof(PreRingOf<NSV, Z, T>) * kWarps, stream>>>( \
+  k_pre<NSV, Z, T><<<blocks_for<kStripHalo>(L.nx, L.ny, seg), kThreads, sizeof(PreRingOf<NSV, Z, T>) * kWarps, stream>>>( \
       uin, fin, fout, uout, uc, rc, L, seg)
 
 cudaError_t launch_stream2d_pre(const float* uin, const float* fin, float* fout, float* uout, float* uc, float* rc,
@@ -550,7 +563,8 @@ template <int NS, bool UPD>
 cudaError_t post_launch(const float* uin, const float* f, const float* uc, float* uout, double* u64,
                         const LevelDesc<float>& L, int seg, cudaStream_t stream) {
   constexpr size_t smem = sizeof(Ring<UPD>) * kWarps;  // > 48 KB for UPD: set by stream2d_prepare
-  k_post<NS, UPD><<<blocks_for(L.nx, L.ny, seg), kThreads, smem, stream>>>(uin, f, uc, uout, u64, L, seg);
+  k_post<NS, UPD><<<blocks_for<post_halo<UPD>()>(L.nx, L.ny, seg), kThreads, smem, stream>>>(uin, f, uc, uout, u64,
+                                                                                            L, seg);
   return cudaGetLastError();
 }
 

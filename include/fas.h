@@ -91,8 +91,8 @@ typedef struct {
   int inner_cycles;      /* FAS_MIXED: FP32 V-cycles per refinement step (default 1)          */
   int use_graph;         /* 1: capture repeated launch sequences in CUDA graphs (default 1)     */
   int path;              /* 0: sweep-fused kernels where the level allows and they pay (default);
-                          * 1: one kernel per operation everywhere, the 3D restriction one
-                          *    coarse cell per thread (reference path);
+                          * 1: one kernel per operation everywhere, the 3D restriction and tau
+                          *    correction one cell per thread (reference path);
                           * 2: sweep-fused kernels on every level they handle, whatever its size */
   int seg_rows;          /* rows per warp segment in the fused 2D kernels (0: default 128)      */
   int location;          /* fas_location (default FAS_CELL). Face grids need kappa == NULL and

@@ -336,7 +336,7 @@ __device__ __forceinline__ void pre_body(PreRingOf<NS, ZERO, TAU>& R, const Stri
         const int s = (it - LR) & M;
         if (FAST || (yr >= 0 && yr < ny)) {
           if (g.lane_out && yr >= g.y0 && yr < g.y1) st4(uout, (int64_t)yr * nx + g.xl, U[s]);
-          if (do_res) {
+          if (do_res && yr >= g.y0 && yr < g.y1) {  // only the segment's own row pairs are restricted
             const float4 r = resid_row<FAST>(U[s], U[(s - 1) & M], U[(s + 1) & M], F[s], yr, q, L);
             if (((it - LR) & 1) == 1) {  // odd row: the pair (yr-1, yr) is complete
               if (g.lane_out && yr - 1 >= g.y0 && yr < g.y1) {

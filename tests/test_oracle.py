@@ -372,6 +372,40 @@ def test_vcycle_exact_coarsest_and_coarsest_sizes():
         np.testing.assert_allclose(u, exact, rtol=0, atol=1e-11 * np.max(np.abs(exact)))
 
 
+@pytest.mark.parametrize("shape,coarsest,exact_c", [((2, 2), 2, True), ((4, 4), 2, False), ((2, 16), 2, True),
+                                                    ((4, 256), 4, True), ((2, 2, 2), 2, True), ((4, 4, 4), 2, False),
+                                                    ((2, 4, 8), 2, True)])
+def test_smallest_and_thinnest_grids_match_dense_solution(shape, coarsest, exact_c):
+    """One-level grids (the shortest axis already at the coarsest size) and two-level ones, with the
+    mixed Dirichlet/Neumann faces of the GPU edge-case tests: the oracle's solve equals the dense
+    solution of A u = f."""
+    bc = (D_, N_, N_, D_, N_, D_)[: 2 * len(shape)]
+    op = cc.Operator(shape, 1.0 / shape[-1], 1.0, 1e-2, 1.0, bc)
+    f = random_field(shape, 281, -1, 1)
+    u = np.zeros(shape)
+    info = cc.solve(cc.build_levels(op, coarsest), u, f,
+                    cc.Params(tol=1e-13, kmax=200, coarsest=coarsest, coarse_exact=exact_c))
+    exact = np.linalg.solve(cc.dense_matrix(op), f.ravel()).reshape(shape)
+    assert info.converged
+    assert np.max(np.abs(u - exact)) <= 1e-12 * np.max(np.abs(exact))
+
+
+def test_zero_rhs_keeps_zero_and_decays_a_guess():
+    """f = 0: from u = 0 the solve stays at 0 exactly; from a random guess it converges to the unique
+    solution 0 (alpha > 0), its residual 1e10 times below the initial one."""
+    shape = (32, 32)
+    op = cc.Operator(shape, 1.0 / 32, 1.0, 1e-3, 1.0, (N_,) * 4)
+    zero = np.zeros(shape)
+    u = np.zeros(shape)
+    info = cc.solve(cc.build_levels(op, 4), u, zero, cc.Params(tol=1e-10, kmax=30, coarsest=4))
+    assert info.converged and not np.any(u)
+    u0 = random_field(shape, 271, -1, 1)
+    u = u0.copy()
+    info = cc.solve(cc.build_levels(op, 4), u, zero, cc.Params(tol=1e-10, kmax=30, coarsest=4))
+    assert info.converged
+    assert cc.norm2(cc.residual(op, u, zero)) <= 1e-10 * cc.norm2(cc.residual(op, u0, zero))
+
+
 def test_singular_neumann_poisson_matches_cosine_transform():
     """Reading G7: alpha = 0 with all-Neumann faces; mean-zero solution of -beta Lap u = f - mean f.
     The cosine transform (DCT-II) diagonalises the operator with eigenvalues beta (lam_x + lam_y)."""
